@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Queue throughput benchmark (one JSON line on stdout).
+
+Workload (one step): the pairwise 50/50 interleaved schedule at its largest
+size, 2^20 threads x 100 operations, capacity 2^20 uint64 slots, seed 0: op i
+of thread t is an enqueue of token (t << 32) | (seq + 1) or a dequeue, as the
+seeded bit schedule says.  One step resets and runs every queue kind (G-LFQ,
+G-WFQ, G-WFQ-YMC) once; the metric is successful (enqueue + dequeue)
+operations per second over the step (Section V-A throughput metric).
+
+Also reported:
+  roofline     the dominant run kernel's algorithmic L2 atomics per second
+               against the same-box measured warp-coalesced 64-bit CAS rate
+  e2e          the same metric through the public batch API with host buffers
+               (pinned host -> device copy of the items, enqueue batch,
+               dequeue batch, device -> host copy of the results)
+  cpu_baseline the oracle's mutex-guarded std::deque on the host cores
+  sweep        kernel-only Mops/s per queue for 2^10 .. 2^20 threads
+
+--impl reference times the oracle's mutex deque (the CPU reference arm).
+Multi-GPU: independent replicas, one per rank, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queue Mops/s (enq+deq) vs threads; % of measured L2-atomic peak; serving p99"
+CAPACITY = 1 << 20
+# DRAM bytes per launch of each run kernel from one ncu capture (profiles/);
+# None until captured for the current kernels.
+NCU_TRAFFIC = {"lfq": None, "wfq": None, "ymc": None}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--threads", type=int, default=1 << 20)
+    p.add_argument("--ops", type=int, default=100)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--kinds", default=None, help="comma list of queue kinds (default: all implemented)")
+    p.add_argument("--no-sweep", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-threads", type=int, default=1 << 17, help="logical threads in the CPU sample")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(device_index)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(T, K, seed, cpu_threads):
+    import oracle
+    Ts = min(T, cpu_threads)
+    sched = __import__("synth").mixed_schedule_bits(seed, Ts, K)
+    cores = os.cpu_count() or 1
+    secs, c, nt = oracle.mutex_run(1, Ts, K, sched=sched, nthreads=cores)
+    succ = int(c[0] + c[2])
+    return {"value": succ / secs / 1e6, "unit": "Mops/s", "cores": nt, "kind": "oracle",
+            "sample": "mutex-guarded std::deque, same 50/50 schedule, first %d of %d threads x %d ops "
+                      "(%d ops, %.2f s)" % (Ts, T, K, Ts * K, secs)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    T, K = args.threads, args.ops
+    Ts = min(T, args.cpu_threads)
+    sched = synth.mixed_schedule_bits(args.seed, Ts, K)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.mutex_run(1, Ts, K, sched=sched, nthreads=cores)
+    tot_s, tot_ops = 0.0, 0
+    for _ in range(args.steps):
+        secs, c, nt = oracle.mutex_run(1, Ts, K, sched=sched, nthreads=cores)
+        tot_s += secs
+        tot_ops += int(c[0] + c[2])
+    v = tot_ops / tot_s / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mops/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "pairwise 50/50 interleaved, %d threads x %d ops, unbounded mutex deque sample"
+                                   % (Ts, K), "threads": Ts, "ops_per_thread": K, "seed": args.seed},
+            "cpu_baseline": {"value": v, "unit": "Mops/s", "cores": cores, "kind": "oracle",
+                             "sample": "first %d of %d logical threads x %d ops per step" % (Ts, T, K)},
+            "e2e": {"value": v, "unit": "Mops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_2606_01693_gb300 as gq
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    T, K = args.threads, args.ops
+    kinds = args.kinds.split(",") if args.kinds else list(gq.READY_KINDS)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- same-box atomic peaks (roofline denominators) ----
+    peak_buf = torch.zeros(1 << 21, dtype=torch.int64, device=dev)     # 16 MiB, L2-resident
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def time_peak(pattern, iters):
+        blocks, threads = sms * 8, 256
+        gq.gq_atomic_peak(pattern, blocks, threads, iters, peak_buf, sink)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gq.gq_atomic_peak(pattern, blocks, threads, iters, peak_buf, sink)
+        e1.record()
+        e1.synchronize()
+        ops = blocks * threads * iters
+        if pattern == gq.GQ_PEAK_SAME_ADDR_FAA:
+            ops //= 32
+        return ops / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+    peaks = {"same_addr_faa_gops": time_peak(gq.GQ_PEAK_SAME_ADDR_FAA, 64),
+             "coalesced_cas_gops": time_peak(gq.GQ_PEAK_COALESCED_CAS, 64),
+             "scattered_cas_gops": time_peak(gq.GQ_PEAK_SCATTERED_CAS, 64),
+             "coalesced_load_gops": time_peak(gq.GQ_PEAK_COALESCED_LOAD, 64)}
+
+    # ---- workload ----
+    sched = synth.mixed_schedule_bits(args.seed, T, K)
+    dsched = torch.from_numpy(sched.view(np.int64)).to(dev)
+    queues = {k: gq.Queue(k, CAPACITY, 8, max_threads=T) for k in kinds}
+    counts = {k: torch.zeros(8, dtype=torch.int64, device=dev) for k in kinds}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    launches_per_step = {"lfq": 3, "wfq": 3, "ymc": 2}
+
+    def step(evs=None):
+        for k in kinds:
+            queues[k].reset()
+            if evs is not None:
+                evs[k][0].record()
+            gq.gq_run(queues[k].handle, gq.GQ_RUN_MIXED, T, block=256, ops=K, sched=dsched, counts=counts[k])
+            if evs is not None:
+                evs[k][1].record()
+
+    for _ in range(args.warmup):
+        step()
+    for k in kinds:
+        st = queues[k].sync_status()
+        if st != 0:
+            raise SystemExit("device error in warm-up: %s" % gq.status_str(st))
+        counts[k].zero_()
+    barrier()
+    clk = Clocks(local)
+    step_ms, kern_ms = [], {k: 0.0 for k in kinds}
+    for _ in range(args.steps):
+        flush.fill_(1)                       # L2 flush between timed steps (256 MiB write)
+        evs = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in kinds}
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        step(evs)
+        s1.record()
+        s1.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        for k in kinds:
+            kern_ms[k] += evs[k][0].elapsed_time(evs[k][1])
+    barrier()
+    clocks = clk.stop()
+    for k in kinds:
+        st = queues[k].sync_status()
+        if st != 0:
+            raise SystemExit("device error: %s" % gq.status_str(st))
+    c = {k: counts[k].cpu().numpy().view(np.uint64) for k in kinds}
+    succ = {k: int(c[k][gq.GQ_CNT_ENQ_OK] + c[k][gq.GQ_CNT_DEQ_OK]) for k in kinds}
+    for k in kinds:
+        assert c[k][gq.GQ_CNT_ERRORS] == 0, k
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        s = torch.tensor([sum(succ.values())], dtype=torch.float64, device=dev)
+        dist.all_reduce(s)
+        all_succ = float(s.item())
+    else:
+        all_succ = float(sum(succ.values()))
+    value = all_succ / (total_ms * 1e-3) / 1e6
+
+    # ---- roofline of the dominant run kernel ----
+    W = 32
+    per_queue = {}
+    for k in kinds:
+        t_s = kern_ms[k] * 1e-3
+        ops_s = succ[k] / t_s
+        slot_rmw = 1.0 if k == "ymc" else 2.0
+        ctr_per_op = (1.0 if k == "ymc" else 2.0) / W
+        atom_rate = ops_s * (slot_rmw + ctr_per_op)
+        peak_atom = peaks["coalesced_cas_gops"] * 1e9
+        counter_ceiling = 2 * W * peaks["same_addr_faa_gops"] * 1e9
+        per_queue[k] = {"kernel_mops": ops_s / 1e6, "kernel_ms_per_launch": kern_ms[k] / args.steps,
+                        "succ_ops_per_launch": succ[k] // args.steps,
+                        "atomics_per_succ_op": slot_rmw + ctr_per_op,
+                        "achieved_gatomic_s": atom_rate / 1e9,
+                        "frac_of_coalesced_cas_peak": atom_rate / peak_atom,
+                        "counter_ceiling_mops": counter_ceiling / 1e6,
+                        "empty": int(c[k][gq.GQ_CNT_DEQ_EMPTY]) // args.steps,
+                        "full": int(c[k][gq.GQ_CNT_ENQ_FULL]) // args.steps}
+    dom = max(kinds, key=lambda k: kern_ms[k])
+    pq = per_queue[dom]
+    traffic = NCU_TRAFFIC.get(dom)
+    roofline = {"bound": "l2_atomic", "kernel": "k_run<u64,%s> (mixed 50/50)" % dom.upper(),
+                "achieved": pq["achieved_gatomic_s"], "peak": peaks["coalesced_cas_gops"],
+                "unit": "Gatomic/s", "frac": pq["frac_of_coalesced_cas_peak"], "traffic": traffic,
+                "peak_source": "measured live: warp-coalesced 64-bit CAS on an L2-resident 16 MiB buffer"}
+
+    # ---- sweep over thread counts (kernel only, untimed region) ----
+    sweep = {}
+    if not args.no_sweep:
+        for k in kinds:
+            sweep[k] = {}
+            for lg in range(10, 21):
+                Ts = 1 << lg
+                if Ts > T:
+                    break
+                sb = torch.from_numpy(synth.mixed_schedule_bits(args.seed, Ts, K).view(np.int64)).to(dev)
+                cc = torch.zeros(8, dtype=torch.int64, device=dev)
+                queues[k].reset()
+                gq.gq_run(queues[k].handle, gq.GQ_RUN_MIXED, Ts, ops=K, sched=sb, counts=cc)
+                queues[k].reset()
+                cc.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                gq.gq_run(queues[k].handle, gq.GQ_RUN_MIXED, Ts, ops=K, sched=sb, counts=cc)
+                e1.record()
+                e1.synchronize()
+                cn = cc.cpu().numpy()
+                sweep[k][str(Ts)] = round((cn[0] + cn[2]) / (e0.elapsed_time(e1) * 1e-3) / 1e6, 1)
+
+    # ---- end to end through the public batch API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        n = CAPACITY
+        host_items = torch.arange(1, n + 1, dtype=torch.int64).pin_memory()
+        host_out = torch.empty(n, dtype=torch.int64).pin_memory()
+        host_cnt = torch.empty(2, dtype=torch.int64).pin_memory()
+        d_items = torch.empty(n, dtype=torch.int64, device=dev)
+        d_out = torch.empty(n, dtype=torch.int64, device=dev)
+        d_cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+
+        def e2e_step():
+            for k in kinds:
+                queues[k].reset()
+                d_items.copy_(host_items, non_blocking=True)
+                gq.gq_enqueue_batch(queues[k].handle, d_items, n, None, d_cnt[0:1])
+                gq.gq_dequeue_batch(queues[k].handle, d_out, n, None, d_cnt[1:2])
+                host_out.copy_(d_out, non_blocking=True)
+                host_cnt.copy_(d_cnt, non_blocking=True)
+            torch.cuda.synchronize()
+            return int(host_cnt[0]) + int(host_cnt[1])
+
+        for _ in range(2):
+            e2e_step()
+        t0 = time.perf_counter()
+        tot = 0
+        for _ in range(args.steps):
+            ok_total = 0
+            for k in kinds:
+                queues[k].reset()
+                d_items.copy_(host_items, non_blocking=True)
+                gq.gq_enqueue_batch(queues[k].handle, d_items, n, None, d_cnt[0:1])
+                gq.gq_dequeue_batch(queues[k].handle, d_out, n, None, d_cnt[1:2])
+                host_out.copy_(d_out, non_blocking=True)
+                host_cnt.copy_(d_cnt, non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+                ok_total += int(host_cnt[0]) + int(host_cnt[1])
+            tot += ok_total
+        dt = time.perf_counter() - t0
+        e2e = {"value": tot / dt / 1e6, "unit": "Mops/s", "h2d_bytes_per_step": 8 * n * len(kinds),
+               "d2h_bytes_per_step": (8 * n + 16) * len(kinds),
+               "how": "per queue: reset, pinned H2D of 2^20 items, gq_enqueue_batch, gq_dequeue_batch, "
+                      "D2H of values and counts; wall clock over %d steps" % args.steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(T, K, args.seed, args.cpu_threads)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mops/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": "pairwise 50/50 interleaved by seed, %d threads x %d ops, capacity 2^20 "
+                                       "uint64, queues %s" % (T, K, "+".join(kinds)),
+                           "threads": T, "ops_per_thread": K, "capacity": CAPACITY, "block": 256, "seed": args.seed,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "flushed between timed steps (256 MiB write); queue state re-initialised inside "
+                                 "each step"},
+                "roofline": roofline, "peaks": peaks, "per_queue": per_queue, "sweep": sweep,
+                "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * sum(launches_per_step[k] for k in kinds),
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

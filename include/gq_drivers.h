@@ -1,0 +1,106 @@
+/*
+ * gq_drivers.h -- C ABI of libgq's workload drivers: the kernels that run the
+ * paper's micro-benchmarks and correctness checks on a queue.
+ *
+ *   gq_run          one kernel in which every thread executes a fixed operation
+ *                   program (Section V-A micro-benchmarks, with the fixed
+ *                   operation counts of the workloads measured here):
+ *                     GQ_RUN_PAIRS  "balanced kernel": each thread repeats
+ *                                   {enqueue; dequeue} `ops / 2` times;
+ *                     GQ_RUN_MIXED  each op is an enqueue or a dequeue as a
+ *                                   seeded bit schedule says (50/50 interleaved);
+ *                     GQ_RUN_SPLIT  "split producer/consumer kernel": the first
+ *                                   `producers` threads only enqueue, the rest
+ *                                   only dequeue; `total_ops` split evenly.
+ *                   Optionally records, per operation, the status, the value and
+ *                   globaltimer timestamps (Section IV: device-recorded histories
+ *                   {proc, op, arg, ret, call, end}).
+ *   gq_run_sequence a single device thread applies an explicit op list (the
+ *                   sequential bit-exactness test against the FIFO specification).
+ *   gq_drain        a single device thread dequeues until EMPTY (FIFO order of
+ *                   the items left behind).
+ *   gq_atomic_peak  same-box L2 atomic micro-benchmarks: the roofline
+ *                   denominators (single-address fetch-add, warp-coalesced and
+ *                   scattered multi-address CAS).
+ *
+ * Payload tokens written by gq_run: 8-byte queues (tid << 32) | (seq + 1)
+ * (Section IV's conformance token); 4-byte queues (tid << 16) | seq, which
+ * requires threads <= 65536 and fewer than 65536 enqueues per thread.
+ * seq counts the thread's enqueue attempts, starting at 0.
+ *
+ * Output arrays are op-major: entry (i * threads + t) is op i of thread t.
+ * Conventions as in gq.h (int status returns, asynchronous on `stream`).
+ */
+#ifndef GQ_DRIVERS_H
+#define GQ_DRIVERS_H
+
+#include <stdint.h>
+
+#include "gq.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { GQ_RUN_PAIRS = 0, GQ_RUN_MIXED = 1, GQ_RUN_SPLIT = 2 };
+
+/* Counter slots accumulated (atomically added) by gq_run into d_counts[8]. */
+enum {
+    GQ_CNT_ENQ_OK = 0, GQ_CNT_ENQ_FULL = 1, GQ_CNT_DEQ_OK = 2, GQ_CNT_DEQ_EMPTY = 3,
+    GQ_CNT_SUM_ENQ = 4,   /* sum (mod 2^64) of successfully enqueued tokens */
+    GQ_CNT_SUM_DEQ = 5,   /* sum (mod 2^64) of successfully dequeued values */
+    GQ_CNT_ERRORS = 6,    /* operations that returned a negative status     */
+    GQ_CNT_RESERVED = 7
+};
+
+typedef struct {
+    uint32_t mode;            /* GQ_RUN_*                                                  */
+    uint32_t threads;         /* logical threads (one device thread each)                 */
+    uint32_t block;           /* threads per block (multiple of 32, <= 1024)               */
+    uint32_t ops;             /* PAIRS/MIXED: operations per thread (PAIRS: even)          */
+    uint32_t producers;       /* SPLIT: threads [0, producers) enqueue                     */
+    uint32_t delay_ns;        /* > 0: each op waits a pseudo-random 0..delay_ns-1 ns first */
+    uint64_t total_ops;       /* SPLIT: operations over all threads                        */
+    const uint64_t* d_sched;  /* MIXED: bit (t * ops + i) set = op i of t is an enqueue   */
+    int8_t* d_status;         /* nullable, op-major                                        */
+    uint64_t* d_val;          /* nullable, op-major: enqueued token / dequeued value       */
+    uint64_t* d_call;         /* nullable, op-major: globaltimer before the op             */
+    uint64_t* d_end;          /* nullable, op-major: globaltimer after the op              */
+    unsigned long long* d_counts; /* 8 words, added to (the caller zeroes them)           */
+} gq_run_args;
+
+/* Launches the driver kernel.  For SPLIT, ops per thread = ceil(total_ops /
+ * threads) bounds the op-major arrays; threads t >= total_ops mod threads do
+ * floor(total_ops / threads) ops.  G-WFQ / G-WFQ-YMC need threads <= max_threads.
+ * Errors: GQ_ERR_INVALID, GQ_ERR_TOO_MANY_THREADS, GQ_ERR_CUDA. */
+int gq_run(gq_handle h, const gq_run_args* args, void* stream);
+
+/* One device thread applies op i = (d_kind[i] == 1 ? enqueue d_val[i] : dequeue)
+ * for i in [0, n), writing d_status[i] and d_out[i] (dequeued value or 0). */
+int gq_run_sequence(gq_handle h, const uint8_t* d_kind, const uint64_t* d_val, uint64_t n,
+                    int8_t* d_status, uint64_t* d_out, void* stream);
+
+/* One device thread dequeues until EMPTY or `max` items; values (zero-extended
+ * to 8 bytes) go to d_out in dequeue order and their number to *d_count. */
+int gq_drain(gq_handle h, uint64_t* d_out, uint64_t max, unsigned long long* d_count, void* stream);
+
+enum {
+    GQ_PEAK_SAME_ADDR_FAA = 0,   /* one lane per warp, fetch-add on one shared word      */
+    GQ_PEAK_COALESCED_CAS = 1,   /* each warp CASes 32 consecutive words (2 lines)       */
+    GQ_PEAK_SCATTERED_CAS = 2,   /* each lane CASes a pseudo-random word                 */
+    GQ_PEAK_COALESCED_LOAD = 3   /* each warp loads 32 consecutive words (reference)     */
+};
+
+/* Runs `iters` rounds of the pattern on a grid of blocks x threads over the
+ * caller's buffer d_buf[0..buf_words) (L2-resident when small enough).  Each
+ * round is one atomic (or load) per participating lane.  d_sink receives a
+ * value derived from the results so the work cannot be elided.
+ * Time it with events on `stream`; ops = blocks * threads * iters (FAA: / 32). */
+int gq_atomic_peak(int pattern, uint32_t blocks, uint32_t threads, uint32_t iters,
+                   unsigned long long* d_buf, uint64_t buf_words, unsigned long long* d_sink,
+                   void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GQ_DRIVERS_H */

@@ -1,0 +1,246 @@
+"""Python binding of libgq: linearizable concurrent FIFO queues on one GB300.
+
+Thin argument marshalling over the C ABI in ``include/gq.h`` and
+``include/gq_drivers.h`` (same function names).  Every queue operation runs in
+the CUDA kernels of ``libgq.so``; PyTorch only supplies device memory and the
+current stream.  There is no CPU fallback: if the library cannot be loaded,
+every call raises.
+
+Queue kinds (Section III of "Scalable Concurrent Queues for GPU"):
+    GQ_LFQ  G-LFQ, bounded lock-free ring with warp-batched tickets
+    GQ_WFQ  G-WFQ, bounded wait-free ring with a cooperative slow path
+    GQ_YMC  G-WFQ-YMC, Yang & Mellor-Crummey queue over a pre-allocated pool
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+GQ_LFQ, GQ_WFQ, GQ_YMC = 0, 1, 2
+KINDS = {"lfq": GQ_LFQ, "wfq": GQ_WFQ, "ymc": GQ_YMC}
+# queue kinds whose device code is complete
+READY_KINDS = ["lfq"]
+GQ_OK, GQ_FULL, GQ_EMPTY = 0, 1, 2
+GQ_ERR_INVALID, GQ_ERR_NOMEM, GQ_ERR_CUDA, GQ_ERR_TIMEOUT = -1, -2, -3, -4
+GQ_ERR_POOL_EXHAUSTED, GQ_ERR_TOO_MANY_THREADS, GQ_ERR_RESERVED_VALUE = -5, -6, -7
+GQ_RUN_PAIRS, GQ_RUN_MIXED, GQ_RUN_SPLIT = 0, 1, 2
+GQ_PEAK_SAME_ADDR_FAA, GQ_PEAK_COALESCED_CAS, GQ_PEAK_SCATTERED_CAS, GQ_PEAK_COALESCED_LOAD = 0, 1, 2, 3
+(GQ_CNT_ENQ_OK, GQ_CNT_ENQ_FULL, GQ_CNT_DEQ_OK, GQ_CNT_DEQ_EMPTY, GQ_CNT_SUM_ENQ, GQ_CNT_SUM_DEQ,
+ GQ_CNT_ERRORS) = range(7)
+
+# Every symbol the headers in include/ declare.
+EXPORTS = [
+    "gq_workspace_bytes", "gq_create", "gq_destroy", "gq_reset", "gq_enqueue_batch", "gq_dequeue_batch",
+    "gq_sync_status", "gq_device_view", "gq_info", "gq_status_str",
+    "gq_run", "gq_run_sequence", "gq_drain", "gq_atomic_peak",
+]
+
+
+class GqError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (what, status_str(status), status))
+
+
+class gq_options(ctypes.Structure):
+    _fields_ = [("cycle_bits", ctypes.c_uint32), ("patience_enq", ctypes.c_uint32),
+                ("patience_deq", ctypes.c_uint32), ("patience_set", ctypes.c_uint32),
+                ("help_delay", ctypes.c_uint32), ("batch_width", ctypes.c_uint32),
+                ("start_ticket", ctypes.c_uint64)]
+
+
+class gq_run_args(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("block", ctypes.c_uint32),
+                ("ops", ctypes.c_uint32), ("producers", ctypes.c_uint32), ("delay_ns", ctypes.c_uint32),
+                ("total_ops", ctypes.c_uint64), ("d_sched", ctypes.c_void_p), ("d_status", ctypes.c_void_p),
+                ("d_val", ctypes.c_void_p), ("d_call", ctypes.c_void_p), ("d_end", ctypes.c_void_p),
+                ("d_counts", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Loads libgq.so (building it first if it is missing or stale).  Raises on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    P, i32, u32, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+    sig = {
+        "gq_workspace_bytes": [i32, u64, u32, u32, P, P],
+        "gq_create": [i32, u64, u32, u32, P, P, P, P],
+        "gq_destroy": [P],
+        "gq_reset": [P, P],
+        "gq_enqueue_batch": [P, P, u64, P, P, P],
+        "gq_dequeue_batch": [P, P, u64, P, P, P],
+        "gq_sync_status": [P, P],
+        "gq_device_view": [P, P],
+        "gq_info": [P, P, P],
+        "gq_status_str": [i32],
+        "gq_run": [P, P, P],
+        "gq_run_sequence": [P, P, P, u64, P, P, P],
+        "gq_drain": [P, P, u64, P, P],
+        "gq_atomic_peak": [i32, u32, u32, u32, P, u64, P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "gq_status_str" else ctypes.c_int
+    _lib = L
+    return L
+
+
+def status_str(s: int) -> str:
+    return load().gq_status_str(int(s)).decode()
+
+
+def _check(s: int, what: str) -> int:
+    if s < 0:
+        raise GqError(s, what)
+    return s
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int | None:
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# C-ABI entry points (same names, raise GqError on a negative status)
+# ---------------------------------------------------------------------------
+
+def gq_workspace_bytes(kind: int, capacity: int, elem_bytes: int, max_threads: int, opt: gq_options | None = None) -> int:
+    out = ctypes.c_uint64(0)
+    _check(load().gq_workspace_bytes(kind, capacity, elem_bytes, max_threads,
+                                     ctypes.byref(opt) if opt else None, ctypes.byref(out)), "gq_workspace_bytes")
+    return out.value
+
+
+def gq_create(kind: int, capacity: int, elem_bytes: int, max_threads: int, opt: gq_options | None = None,
+              workspace=None, stream=None) -> int:
+    h = ctypes.c_void_p(0)
+    _check(load().gq_create(kind, capacity, elem_bytes, max_threads, ctypes.byref(opt) if opt else None,
+                            _ptr(workspace), _stream(stream), ctypes.byref(h)), "gq_create")
+    return h.value
+
+
+def gq_destroy(h: int) -> None:
+    _check(load().gq_destroy(h), "gq_destroy")
+
+
+def gq_reset(h: int, stream=None) -> None:
+    _check(load().gq_reset(h, _stream(stream)), "gq_reset")
+
+
+def gq_enqueue_batch(h: int, items, n: int | None = None, status=None, num_ok=None, stream=None) -> None:
+    n = items.numel() if n is None else n
+    _check(load().gq_enqueue_batch(h, _ptr(items), n, _ptr(status), _ptr(num_ok), _stream(stream)),
+           "gq_enqueue_batch")
+
+
+def gq_dequeue_batch(h: int, out, n: int | None = None, status=None, num_ok=None, stream=None) -> None:
+    n = out.numel() if n is None else n
+    _check(load().gq_dequeue_batch(h, _ptr(out), n, _ptr(status), _ptr(num_ok), _stream(stream)),
+           "gq_dequeue_batch")
+
+
+def gq_sync_status(h: int, stream=None) -> int:
+    """Synchronises the stream and returns (and clears) the latched device error status."""
+    return load().gq_sync_status(h, _stream(stream))
+
+
+def gq_info(h: int) -> tuple[int, bool]:
+    b, o = ctypes.c_uint64(0), ctypes.c_int(0)
+    _check(load().gq_info(h, ctypes.byref(b), ctypes.byref(o)), "gq_info")
+    return b.value, bool(o.value)
+
+
+def gq_run(h: int, mode: int, threads: int, block: int = 256, ops: int = 0, producers: int = 0,
+           total_ops: int = 0, sched=None, status=None, val=None, call=None, end=None, counts=None,
+           delay_ns: int = 0, stream=None) -> None:
+    a = gq_run_args(mode, threads, block, ops, producers, delay_ns, total_ops, _ptr(sched), _ptr(status),
+                    _ptr(val), _ptr(call), _ptr(end), _ptr(counts))
+    _check(load().gq_run(h, ctypes.byref(a), _stream(stream)), "gq_run")
+
+
+def gq_run_sequence(h: int, kind, val, status, out, stream=None) -> None:
+    _check(load().gq_run_sequence(h, _ptr(kind), _ptr(val), kind.numel(), _ptr(status), _ptr(out),
+                                  _stream(stream)), "gq_run_sequence")
+
+
+def gq_drain(h: int, out, count, max_items: int | None = None, stream=None) -> None:
+    m = out.numel() if max_items is None else max_items
+    _check(load().gq_drain(h, _ptr(out), m, _ptr(count), _stream(stream)), "gq_drain")
+
+
+def gq_atomic_peak(pattern: int, blocks: int, threads: int, iters: int, buf, sink, stream=None) -> None:
+    _check(load().gq_atomic_peak(pattern, blocks, threads, iters, _ptr(buf), buf.numel(), _ptr(sink),
+                                 _stream(stream)), "gq_atomic_peak")
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Queue:
+    """Owns one libgq queue handle.  All methods are asynchronous on the current stream."""
+
+    def __init__(self, kind, capacity: int, elem_bytes: int = 8, max_threads: int = 1 << 20,
+                 use_torch_memory: bool = False, **options):
+        self.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+        self.capacity = capacity
+        self.elem_bytes = elem_bytes
+        self.max_threads = max_threads
+        self.opt = gq_options(**options) if options else None
+        if "patience_enq" in options or "patience_deq" in options:
+            self.opt.patience_set = 1
+        self._ws = None
+        if use_torch_memory:
+            import torch
+            nbytes = gq_workspace_bytes(self.kind, capacity, elem_bytes, max_threads, self.opt)
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            addr = (self._ws.data_ptr() + 255) // 256 * 256
+            self.handle = gq_create(self.kind, capacity, elem_bytes, max_threads, self.opt, addr)
+        else:
+            self.handle = gq_create(self.kind, capacity, elem_bytes, max_threads, self.opt)
+
+    def reset(self, stream=None):
+        gq_reset(self.handle, stream)
+
+    def enqueue(self, items, status=None, num_ok=None, stream=None):
+        gq_enqueue_batch(self.handle, items, None, status, num_ok, stream)
+
+    def dequeue(self, out, status=None, num_ok=None, stream=None):
+        gq_dequeue_batch(self.handle, out, None, status, num_ok, stream)
+
+    def sync_status(self, stream=None) -> int:
+        return gq_sync_status(self.handle, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gq_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,208 @@
+// Workload drivers (include/gq_drivers.h): the micro-benchmark kernels of
+// Section V-A and the recorders used by the correctness checks of Section IV.
+#include <cuda_runtime.h>
+
+#include "../../include/gq_drivers.h"
+#include "gq_host.h"
+#include "gq_ops.cuh"
+
+using namespace gqd;
+
+namespace {
+
+struct RunK {
+    u32 mode, threads, ops, producers, delay_ns;
+    u64 total_ops;
+    const u64* sched;
+    int8_t* status;
+    u64* val;
+    u64* call;
+    u64* end;
+    unsigned long long* counts;
+};
+
+__device__ __forceinline__ u32 mix32(u32 a, u32 b) {
+    u32 h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u);
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    return h;
+}
+
+template <class T, int KIND>
+__global__ void k_run(gq_dev q, RunK a) {
+    const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
+    u64 c_enq_ok = 0, c_full = 0, c_deq_ok = 0, c_empty = 0, s_enq = 0, s_deq = 0, c_err = 0;
+    if (t < a.threads) {
+        u32 nops = a.ops;
+        bool producer = true;
+        if (a.mode == GQ_RUN_SPLIT) {
+            nops = (u32)(a.total_ops / a.threads) + (t < (u32)(a.total_ops % a.threads) ? 1u : 0u);
+            producer = t < a.producers;
+        }
+        u32 seq = 0;
+        for (u32 i = 0; i < nops; ++i) {
+            bool is_enq;
+            if (a.mode == GQ_RUN_PAIRS) {
+                is_enq = !(i & 1u);
+            } else if (a.mode == GQ_RUN_MIXED) {
+                const u64 j = (u64)t * a.ops + i;
+                is_enq = (a.sched[j >> 6] >> (j & 63)) & 1ull;
+            } else {
+                is_enq = producer;
+            }
+            if (a.delay_ns) __nanosleep(mix32(t, i) % a.delay_ns);
+            const u64 tc = a.call ? globaltimer() : 0;
+            int s;
+            u64 v;
+            if (is_enq) {
+                v = (sizeof(T) == 4) ? (((u64)t << 16) | seq) : (((u64)t << 32) | (u64)(seq + 1));
+                ++seq;
+                s = queue_enqueue<T, KIND>(q, (T)v, t);
+                if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
+                else if (s == GQ_FULL) ++c_full;
+                else ++c_err;
+            } else {
+                T x = 0;
+                s = queue_dequeue<T, KIND>(q, &x, t);
+                v = (s == GQ_OK) ? (u64)x : 0;
+                if (s == GQ_OK) { ++c_deq_ok; s_deq += v; }
+                else if (s == GQ_EMPTY) ++c_empty;
+                else ++c_err;
+            }
+            const u64 j = (u64)i * a.threads + t;
+            if (a.end) a.end[j] = globaltimer();
+            if (a.call) a.call[j] = tc;
+            if (a.status) a.status[j] = (int8_t)s;
+            if (a.val) a.val[j] = v;
+        }
+    }
+    warp_add_full(&a.counts[GQ_CNT_ENQ_OK], c_enq_ok);
+    warp_add_full(&a.counts[GQ_CNT_ENQ_FULL], c_full);
+    warp_add_full(&a.counts[GQ_CNT_DEQ_OK], c_deq_ok);
+    warp_add_full(&a.counts[GQ_CNT_DEQ_EMPTY], c_empty);
+    warp_add_full(&a.counts[GQ_CNT_SUM_ENQ], s_enq);
+    warp_add_full(&a.counts[GQ_CNT_SUM_DEQ], s_deq);
+    warp_add_full(&a.counts[GQ_CNT_ERRORS], c_err);
+}
+
+template <class T, int KIND>
+__global__ void k_sequence(gq_dev q, const uint8_t* kind, const u64* val, u64 n, int8_t* status, u64* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (u64 i = 0; i < n; ++i) {
+        int s;
+        u64 r = 0;
+        if (kind[i] == 1) {
+            s = queue_enqueue<T, KIND>(q, (T)val[i], 0);
+        } else {
+            T x = 0;
+            s = queue_dequeue<T, KIND>(q, &x, 0);
+            if (s == GQ_OK) r = (u64)x;
+        }
+        status[i] = (int8_t)s;
+        out[i] = r;
+    }
+}
+
+template <class T, int KIND>
+__global__ void k_drain(gq_dev q, u64* out, u64 max, unsigned long long* count) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    u64 k = 0;
+    while (k < max) {
+        T x = 0;
+        const int s = queue_dequeue<T, KIND>(q, &x, 0);
+        if (s != GQ_OK) break;
+        out[k++] = (u64)x;
+    }
+    *count = k;
+}
+
+template <class T, int KIND>
+int launch_run(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
+    const u32 grid = (a.threads + block - 1) / block;
+    k_run<T, KIND><<<grid, block, 0, st>>>(h->dev, a);
+    return gq_check_launch();
+}
+
+template <class T>
+int dispatch_run(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
+    switch (h->dev.kind) {
+        case GQ_LFQ: return launch_run<T, GQ_LFQ>(h, a, block, st);
+        case GQ_WFQ: return launch_run<T, GQ_WFQ>(h, a, block, st);
+        default: return launch_run<T, GQ_YMC>(h, a, block, st);
+    }
+}
+
+template <class T>
+int dispatch_seq(gq_queue* h, const uint8_t* kind, const u64* val, u64 n, int8_t* status, u64* out,
+                 cudaStream_t st) {
+    switch (h->dev.kind) {
+        case GQ_LFQ: k_sequence<T, GQ_LFQ><<<1, 1, 0, st>>>(h->dev, kind, val, n, status, out); break;
+        case GQ_WFQ: k_sequence<T, GQ_WFQ><<<1, 1, 0, st>>>(h->dev, kind, val, n, status, out); break;
+        default: k_sequence<T, GQ_YMC><<<1, 1, 0, st>>>(h->dev, kind, val, n, status, out); break;
+    }
+    return gq_check_launch();
+}
+
+template <class T>
+int dispatch_drain(gq_queue* h, u64* out, u64 max, unsigned long long* count, cudaStream_t st) {
+    switch (h->dev.kind) {
+        case GQ_LFQ: k_drain<T, GQ_LFQ><<<1, 1, 0, st>>>(h->dev, out, max, count); break;
+        case GQ_WFQ: k_drain<T, GQ_WFQ><<<1, 1, 0, st>>>(h->dev, out, max, count); break;
+        default: k_drain<T, GQ_YMC><<<1, 1, 0, st>>>(h->dev, out, max, count); break;
+    }
+    return gq_check_launch();
+}
+
+}  // namespace
+
+extern "C" int gq_run(gq_handle h, const gq_run_args* args, void* stream) {
+    if (!h || !args || !args->d_counts) return GQ_ERR_INVALID;
+    const gq_run_args& g = *args;
+    if (g.mode > GQ_RUN_SPLIT || g.threads == 0) return GQ_ERR_INVALID;
+    if (g.block == 0 || g.block > 1024 || (g.block & 31)) return GQ_ERR_INVALID;
+    if (g.mode == GQ_RUN_MIXED && !g.d_sched) return GQ_ERR_INVALID;
+    if (g.mode == GQ_RUN_PAIRS && (g.ops & 1)) return GQ_ERR_INVALID;
+    if (g.mode == GQ_RUN_SPLIT && (g.producers > g.threads || g.total_ops / g.threads >= (1ull << 32)))
+        return GQ_ERR_INVALID;
+    if (h->dev.kind != GQ_LFQ && g.threads > h->dev.max_threads) return GQ_ERR_TOO_MANY_THREADS;
+    if (h->dev.elem_bytes == 4) {
+        const uint64_t per = (g.mode == GQ_RUN_SPLIT) ? (g.total_ops + g.threads - 1) / g.threads : g.ops;
+        if (g.threads > 65536 || per > 65536) return GQ_ERR_INVALID;
+    }
+    RunK a;
+    a.mode = g.mode;
+    a.threads = g.threads;
+    a.ops = g.ops;
+    a.producers = g.producers;
+    a.delay_ns = g.delay_ns;
+    a.total_ops = g.total_ops;
+    a.sched = reinterpret_cast<const u64*>(g.d_sched);
+    a.status = g.d_status;
+    a.val = reinterpret_cast<u64*>(g.d_val);
+    a.call = reinterpret_cast<u64*>(g.d_call);
+    a.end = reinterpret_cast<u64*>(g.d_end);
+    a.counts = g.d_counts;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return h->dev.elem_bytes == 4 ? dispatch_run<unsigned int>(h, a, g.block, st)
+                                  : dispatch_run<unsigned long long>(h, a, g.block, st);
+}
+
+extern "C" int gq_run_sequence(gq_handle h, const uint8_t* d_kind, const uint64_t* d_val, uint64_t n,
+                               int8_t* d_status, uint64_t* d_out, void* stream) {
+    if (!h || (n && (!d_kind || !d_val || !d_status || !d_out))) return GQ_ERR_INVALID;
+    if (n == 0) return GQ_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const u64* val = reinterpret_cast<const u64*>(d_val);
+    u64* out = reinterpret_cast<u64*>(d_out);
+    return h->dev.elem_bytes == 4 ? dispatch_seq<unsigned int>(h, d_kind, val, n, d_status, out, st)
+                                  : dispatch_seq<unsigned long long>(h, d_kind, val, n, d_status, out, st);
+}
+
+extern "C" int gq_drain(gq_handle h, uint64_t* d_out, uint64_t max, unsigned long long* d_count, void* stream) {
+    if (!h || !d_count || (max && !d_out)) return GQ_ERR_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    u64* out = reinterpret_cast<u64*>(d_out);
+    return h->dev.elem_bytes == 4 ? dispatch_drain<unsigned int>(h, out, max, d_count, st)
+                                  : dispatch_drain<unsigned long long>(h, out, max, d_count, st);
+}

@@ -1,0 +1,50 @@
+// Host-side internals shared by the translation units of libgq (not part of
+// the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gq.h"
+
+// Per-thread record sizes (bytes, one or more 128-byte lines).
+constexpr uint64_t kWfqRecBytes = 128;
+constexpr uint64_t kYmcRecBytes = 128;
+constexpr uint64_t kLine = 128;
+
+struct gq_layout {
+    uint64_t ctrl;       // control lines (error word, scratch, counters, thresholds)
+    uint64_t aq_slots, fq_slots, data;
+    uint64_t aq_rec, fq_rec, aq_owner, fq_owner;
+    uint64_t cell_val, cell_enq, cell_deq, ymc_rec;
+    uint64_t total;
+};
+
+// Control-region line indices.
+enum {
+    kCtlErr = 0,
+    kCtlScratch = 1,
+    kCtlAqHead = 2, kCtlAqTail = 3, kCtlAqThr = 4,
+    kCtlFqHead = 5, kCtlFqTail = 6, kCtlFqThr = 7,
+    kCtlYmcTail = 8, kCtlYmcHead = 9,
+    kCtlLines = 16
+};
+
+struct gq_queue {
+    gq_dev dev;
+    gq_layout lay;
+    gq_options opt;
+    void* ws;
+    bool owned;
+    int device;
+    int sm_count;
+    uint64_t start_ticket;
+};
+
+// Status helpers
+int gq_check_launch();
+
+// Launch configuration for a grid-stride kernel whose threads need one record
+// each (G-WFQ, G-WFQ-YMC): never more threads than records.
+void gq_grid_for(const gq_queue* q, uint64_t n_items, int occupancy_blocks_per_sm, uint32_t block,
+                 uint32_t* grid_out);

@@ -1,0 +1,182 @@
+// G-LFQ: bounded lock-free ring with warp-batched tickets (Section III-B,
+// Algorithm 1), and the index-indirection layer around it.
+//
+// Inner ring ("Data structure", Section III-B): 2n physical slots, logical
+// capacity n, monotonically increasing Head and Tail tickets, a Threshold for
+// empty detection.  Ticket t maps to slot(t) = t mod 2n and
+// cycle(t) = floor(t / 2n) mod R, R = 2^cycle_bits.  Each slot is one 64-bit word
+//     bits 63..33  Cycle (cycle_bits <= 31 wide, the rest zero)
+//     bit  32      Safe
+//     bits 31..0   Index:  a value < 2^32 - 2,  BOT = 2^32 - 1 (empty),
+//                          BOTC = 2^32 - 2 (consumed)
+// Consume is an atomic OR of BOTC into the index bits: any index becomes BOTC
+// or BOT, both of the "empty class", and the Cycle and Safe bits are kept.
+// Cycles are compared modulo R (a is older than b iff 0 < (b - a) mod R < R/2),
+// sound while the live skew on a slot stays below R/2 (Lemma "Reduced-width
+// cycle tags").
+//
+// The ring itself does not detect FULL: it relies on never holding more than n
+// indices.  The outer queue guarantees that: "fq" starts full with 0..n-1, "aq"
+// starts empty, and every user enqueue first takes a free index from fq
+// (none left = FULL), stores the payload at data[index] and puts the index in
+// aq; a dequeue takes an index from aq, reads the payload and returns the
+// index to fq (Section III-B "outer indirection layer that moves indices").
+//
+// GPU-first choices (differences from the CPU sCQ ring):
+//   * tickets of one warp are consecutive, so the 32 slot RMWs of a warp hit two
+//     adjacent 128-byte lines and coalesce into few L2 atomic requests; sCQ's
+//     cache-line remapping of consecutive tickets is deliberately not used;
+//   * a CAS that fails on a slot re-evaluates the same ticket with the value it
+//     returned (no ticket is burned for a lost race on a still-usable slot).
+#pragma once
+
+#include "gq_atomics.cuh"
+
+namespace gqd {
+
+constexpr u64 kSafe = 1ull << 32;
+constexpr u32 kBot = 0xFFFFFFFFu;
+constexpr u32 kBotC = 0xFFFFFFFEu;
+
+struct RingGeom {
+    u32 order;       // log2(2n)
+    u32 width;       // WaveFAA group width
+    u64 smask;       // 2n - 1
+    u64 cmask;       // R - 1
+    u64 half;        // R / 2
+    i64 thr_reset;   // 3n - 1
+};
+
+__device__ __forceinline__ RingGeom ring_geom(const gq_dev& q) {
+    RingGeom g;
+    g.order = q.log2n + 1;
+    g.width = q.batch_width;
+    g.smask = (2ull << q.log2n) - 1;
+    g.cmask = (1ull << q.cycle_bits) - 1;
+    g.half = 1ull << (q.cycle_bits - 1);
+    g.thr_reset = (i64)(3ull << q.log2n) - 1;
+    return g;
+}
+
+// a is strictly older than b (modular, Lemma on cycle tags)
+__device__ __forceinline__ bool cyc_older(u64 a, u64 b, const RingGeom& g) {
+    const u64 d = (b - a) & g.cmask;
+    return d != 0 && d < g.half;
+}
+
+__device__ __forceinline__ u64 lfq_cycle(u64 e) { return e >> 33; }
+__device__ __forceinline__ u32 lfq_index(u64 e) { return (u32)e; }
+__device__ __forceinline__ u64 lfq_entry(u64 cyc, u64 safe, u32 idx) { return (cyc << 33) | safe | idx; }
+
+// Catch Tail up to at least `head` (Algorithm 1 TryDeq, "catch up Tail").
+__device__ __forceinline__ void ring_catchup(const gq_ring_view& r, u64 tail, u64 head) {
+    for (u32 it = 0; it < kRetryLimit; ++it) {
+        if (cas(r.tail, tail, head)) return;
+        head = ld_rlx(r.head);
+        tail = ld_rlx(r.tail);
+        if ((i64)(tail - head) >= 0) return;
+    }
+}
+
+// Inner-ring enqueue of index `idx` (TryEnq of Algorithm 1, retried until it
+// succeeds).  Returns GQ_OK, or GQ_ERR_TIMEOUT if the retry bound expires.
+template <bool MATCH>
+__device__ int lfq_ring_enq(const gq_ring_view& r, const RingGeom& g, u32 idx, unsigned int* err) {
+    for (u32 it = 0; it < kRetryLimit; ++it) {
+        const u64 t = warp_faa<MATCH>(r.tail, 1, g.width);
+        u64* slot = r.slots + (t & g.smask);
+        const u64 c = (t >> g.order) & g.cmask;
+        u64 e = ld_acq(slot);
+        for (;;) {
+            if (!cyc_older(lfq_cycle(e), c, g) || lfq_index(e) < kBotC) break;
+            if (!(e & kSafe)) {
+                // an unsafe slot may be reused only if no dequeuer has passed t
+                if ((i64)(ld_rlx(r.head) - t) > 0) break;
+            }
+            if (cas(slot, e, lfq_entry(c, kSafe, idx))) {
+                if (ld_rlx(r.threshold) != g.thr_reset) {
+                    if (exch(r.threshold, g.thr_reset) == INT64_MIN) latch_error(err, GQ_ERR_INVALID);
+                }
+                return GQ_OK;
+            }
+            // CAS lost: e holds the current entry; re-evaluate the same ticket
+        }
+    }
+    latch_error(err, GQ_ERR_TIMEOUT);
+    return GQ_ERR_TIMEOUT;
+}
+
+// Inner-ring dequeue (TryDeq of Algorithm 1, retried while it returns RETRY).
+// Returns GQ_OK with *idx, GQ_EMPTY, or GQ_ERR_TIMEOUT.
+template <bool MATCH>
+__device__ int lfq_ring_deq(const gq_ring_view& r, const RingGeom& g, u32* idx, unsigned int* err) {
+    if (ld_rlx(r.threshold) < 0) return GQ_EMPTY;
+    for (u32 it = 0; it < kRetryLimit; ++it) {
+        const u64 h = warp_faa<MATCH>(r.head, 1, g.width);
+        u64* slot = r.slots + (h & g.smask);
+        const u64 c = (h >> g.order) & g.cmask;
+        u64 e = ld_acq(slot);
+        for (;;) {
+            const u64 ec = lfq_cycle(e);
+            if (ec == c) {
+                if (lfq_index(e) < kBotC) {          // Consume and return the index
+                    const u64 before = fetch_or(slot, kBotC);
+                    *idx = lfq_index(before);
+                    return GQ_OK;
+                }
+                break;
+            }
+            if (!cyc_older(ec, c, g)) break;         // slot already belongs to a later cycle
+            // empty class: advance the slot to cycle c (still empty);
+            // occupied by an older cycle: clear Safe so the enqueuer of t = h
+            // does not reuse it once Head has passed h.
+            const u64 ne = (lfq_index(e) >= kBotC) ? lfq_entry(c, e & kSafe, kBot) : (e & ~kSafe);
+            if (cas(slot, e, ne)) break;
+        }
+        const u64 tl = ld_rlx(r.tail);
+        if ((i64)(tl - (h + 1)) <= 0) {
+            ring_catchup(r, tl, h + 1);
+            faa(r.threshold, -1);
+            return GQ_EMPTY;
+        }
+        if (faa(r.threshold, -1) <= 0) return GQ_EMPTY;
+    }
+    latch_error(err, GQ_ERR_TIMEOUT);
+    return GQ_ERR_TIMEOUT;
+}
+
+// ---------------------------------------------------------------------------
+// Outer queue over two rings (indirection layer)
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void data_store(const gq_dev& q, u32 i, T v) {
+    aref<T>(static_cast<T*>(q.data)[i]).store(v, kRlx);
+}
+template <class T>
+__device__ __forceinline__ T data_load(const gq_dev& q, u32 i) {
+    return aref<T>(static_cast<T*>(q.data)[i]).load(kRlx);
+}
+
+template <class T, bool MATCH>
+__device__ int lfq_enqueue(const gq_dev& q, T v) {
+    const RingGeom g = ring_geom(q);
+    u32 i;
+    int s = lfq_ring_deq<MATCH>(q.fq, g, &i, q.err);
+    if (s == GQ_EMPTY) return GQ_FULL;
+    if (s != GQ_OK) return s;
+    data_store<T>(q, i, v);                           // ordered before the release CAS in aq
+    return lfq_ring_enq<MATCH>(q.aq, g, i, q.err);
+}
+
+template <class T, bool MATCH>
+__device__ int lfq_dequeue(const gq_dev& q, T* v) {
+    const RingGeom g = ring_geom(q);
+    u32 i;
+    int s = lfq_ring_deq<MATCH>(q.aq, g, &i, q.err);
+    if (s != GQ_OK) return s;
+    *v = data_load<T>(q, i);                          // after the acquire on the aq slot
+    s = lfq_ring_enq<MATCH>(q.fq, g, i, q.err);       // release: the read precedes reuse
+    return s == GQ_OK ? GQ_OK : s;
+}
+
+}  // namespace gqd

@@ -1,0 +1,211 @@
+"""GPU parity tests: the CUDA queues against the CPU oracle (run with -m gpu).
+
+Every test calls the CUDA path through the C ABI (libgq.so) and checks the
+results with the oracle, which shares no code with it:
+  * sequential bit-exactness against the FIFO specification (FULL at exactly n
+    items, EMPTY at exactly 0, ring and cycle-tag wrap-around);
+  * the one-block pairs workload (256 threads x 1000 enqueue-then-dequeue pairs,
+    capacity 2^10, 32-bit tokens): zero EMPTY, zero FULL, exactly once,
+    per-producer order;
+  * the 50/50 interleaved workload up to 2^20 threads x 100 ops at capacity
+    2^20 and the imbalanced producer/consumer workload (2^18 threads, 10^7 ops,
+    capacity 2^16) with the run-log invariant checks;
+  * linearizability of tiny recorded histories (Wing & Gong);
+  * the host batch API (exactly once through gq_enqueue_batch/gq_dequeue_batch).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2606_01693_gb300 as gq
+import synth
+
+from gpu_util import DEV, drain, make_queue, run_log, u64
+
+pytestmark = pytest.mark.gpu
+
+KINDS = list(gq.READY_KINDS)
+
+
+def _seq_ops(seed, n, cap, p_enq):
+    kinds, vals = synth.random_op_list(seed, n, p_enq)
+    return kinds, vals
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("cap,cycle_bits,seed,p", [(2, 0, 1, 0.5), (2, 3, 2, 0.55), (4, 3, 3, 0.5),
+                                                  (16, 0, 4, 0.6), (16, 3, 5, 0.45), (1024, 0, 6, 0.5)])
+@pytest.mark.parametrize("elem", [4, 8])
+def test_sequential_bit_exact(kind, cap, cycle_bits, seed, p, elem):
+    n = 4000
+    kinds, vals = _seq_ops(seed, n, cap, p)
+    if elem == 4:
+        vals = vals & np.uint64(0xFFFFFFFF)
+    q = make_queue(kind, cap, elem, max_threads=64, cycle_bits=cycle_bits)
+    dk = torch.from_numpy(kinds).to(DEV)
+    dv = torch.from_numpy(vals.view(np.int64)).to(DEV)
+    ds = torch.zeros(n, dtype=torch.int8, device=DEV)
+    do = torch.zeros(n, dtype=torch.int64, device=DEV)
+    gq.gq_run_sequence(q.handle, dk, dv, ds, do)
+    assert q.sync_status() == 0
+    want_s, want_o, final = oracle.seqfifo_run(cap, kinds, vals)
+    got_s = ds.cpu().numpy()
+    got_o = u64(do)
+    assert (got_s == want_s).all(), np.flatnonzero(got_s != want_s)[:5]
+    assert (got_o == want_o).all()
+    assert (drain(q, cap) == final).all()
+    # FULL exactly at n items, EMPTY exactly at 0 (the spec's boundaries) were crossed
+    assert (want_s == 1).any() and (want_s == 2).any()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_sequential_counter_wrap(kind):
+    # counters start 3 * 2n tickets before 2^64 (G-LFQ) so ticket arithmetic wraps mid-run
+    cap = 8
+    start = (1 << 64) - 4 * 2 * cap if kind == "lfq" else (1 << 43) - 4 * 2 * cap
+    kinds, vals = _seq_ops(11, 3000, cap, 0.5)
+    q = make_queue(kind, cap, 8, max_threads=64, start_ticket=start)
+    dk = torch.from_numpy(kinds).to(DEV)
+    dv = torch.from_numpy(vals.view(np.int64)).to(DEV)
+    ds = torch.zeros(len(kinds), dtype=torch.int8, device=DEV)
+    do = torch.zeros(len(kinds), dtype=torch.int64, device=DEV)
+    gq.gq_run_sequence(q.handle, dk, dv, ds, do)
+    assert q.sync_status() == 0
+    want_s, want_o, final = oracle.seqfifo_run(cap, kinds, vals)
+    assert (ds.cpu().numpy() == want_s).all()
+    assert (u64(do) == want_o).all()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("width", [32, 1])
+def test_pairs_one_block(kind, width):
+    # 1 block x 256 threads, 1000 enqueue-then-dequeue pairs each, capacity 2^10, u32 tokens (t << 16) | seq
+    T, pairs = 256, 1000
+    q = make_queue(kind, 1 << 10, 4, max_threads=T, batch_width=width)
+    r = run_log(q, gq.GQ_RUN_PAIRS, T, 2 * pairs)
+    c = r["counts"]
+    assert c[gq.GQ_CNT_ENQ_OK] == T * pairs and c[gq.GQ_CNT_DEQ_OK] == T * pairs
+    assert c[gq.GQ_CNT_ENQ_FULL] == 0 and c[gq.GQ_CNT_DEQ_EMPTY] == 0   # balanced closed form
+    assert c[gq.GQ_CNT_ERRORS] == 0
+    assert c[gq.GQ_CNT_SUM_ENQ] == c[gq.GQ_CNT_SUM_DEQ]
+    left = drain(q, 1 << 10)
+    assert len(left) == 0
+    rep = oracle.check_log(r["kind"], r["status"], r["val"], left, prod_shift=16, seq_mask=0xFFFF, seq_bias=0)
+    assert rep["violations"] == 0, rep
+    assert rep["deq_ok"] == T * pairs
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("T", [1 << 10, 1 << 14])
+def test_mixed_interleaved(kind, T):
+    K = 100
+    sched = synth.mixed_schedule_bits(0, T, K)
+    q = make_queue(kind, 1 << 20, 8, max_threads=T)
+    r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched)
+    left = drain(q, 1 << 20)
+    rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
+    assert rep["violations"] == 0, rep
+    assert rep["enq_full"] == 0
+    assert rep["enq_ok"] == int(synth.schedule_is_enq(sched, T, K).sum())
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_mixed_full_size(kind):
+    # the largest configuration of the throughput sweep: 2^20 threads x 100 ops, capacity 2^20
+    T, K = 1 << 20, 100
+    sched = synth.mixed_schedule_bits(0, T, K)
+    q = make_queue(kind, 1 << 20, 8, max_threads=T)
+    r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched)
+    left = drain(q, 1 << 20)
+    rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
+    assert rep["violations"] == 0, rep
+    c = r["counts"]
+    assert c[gq.GQ_CNT_ERRORS] == 0
+    assert (int(c[gq.GQ_CNT_SUM_ENQ]) - int(c[gq.GQ_CNT_SUM_DEQ]) - int(left.sum(dtype=np.uint64))) % (1 << 64) == 0
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("frac", [0.1, 0.5, 0.9])
+def test_split_producer_consumer(kind, frac):
+    T, total, cap = 1 << 18, 10 ** 7, 1 << 16
+    P = int(frac * T)
+    q = make_queue(kind, cap, 8, max_threads=T)
+    r = run_log(q, gq.GQ_RUN_SPLIT, T, producers=P, total_ops=total)
+    left = drain(q, cap)
+    rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
+    assert rep["violations"] == 0, rep
+    assert rep["enq_ok"] + rep["enq_full"] == int(synth.split_ops_per_thread(total, T)[:P].sum())
+    assert len(left) <= cap
+    if frac == 0.9:
+        assert rep["enq_full"] > 0          # the bounded queue filled up
+    if frac == 0.1:
+        assert rep["deq_empty"] > 0
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("cap", [2, 4])
+def test_tiny_histories_linearizable(kind, cap):
+    rng = np.random.default_rng(cap)
+    checked = 0
+    for trial in range(60):
+        T = int(rng.integers(2, 7))
+        K = int(rng.integers(2, 5))
+        if T * K > 24:
+            K = 24 // T
+        sched = synth.mixed_schedule_bits(1000 + trial, T, K)
+        q = make_queue(kind, cap, 8, max_threads=64)
+        r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched, block=32, timestamps=True,
+                    delay_ns=int(rng.integers(0, 3000)))
+        m = r["kind"].reshape(-1) != 255
+        op = r["kind"].reshape(-1)[m]
+        res = oracle.linearizable(op, r["val"].reshape(-1)[m], r["status"].reshape(-1)[m],
+                                  r["call"].reshape(-1)[m], r["end"].reshape(-1)[m], cap=cap)
+        assert res == 1, (trial, r)
+        checked += 1
+        q.close()
+    assert checked == 60
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("elem", [4, 8])
+def test_batch_api_exactly_once(kind, elem):
+    cap = 1 << 12
+    q = make_queue(kind, cap, elem, max_threads=1 << 16)
+    dt = torch.int32 if elem == 4 else torch.int64
+    n = cap + 1000                                        # 1000 attempts must fail FULL
+    items = torch.arange(1, n + 1, dtype=dt, device=DEV) * 7
+    st = torch.zeros(n, dtype=torch.int8, device=DEV)
+    ok = torch.zeros(1, dtype=torch.int64, device=DEV)
+    q.enqueue(items, st, ok)
+    assert q.sync_status() == 0
+    assert int(ok.item()) == cap
+    s = st.cpu().numpy()
+    assert (s == 0).sum() == cap and (s == 1).sum() == n - cap
+    out = torch.zeros(n, dtype=dt, device=DEV)
+    st2 = torch.zeros(n, dtype=torch.int8, device=DEV)
+    ok2 = torch.zeros(1, dtype=torch.int64, device=DEV)
+    q.dequeue(out, st2, ok2)
+    assert q.sync_status() == 0
+    k = int(ok2.item())
+    assert k == cap and (st2.cpu().numpy() == 2).sum() == n - cap
+    got = np.sort(out[:k].cpu().numpy())
+    want = np.sort(items.cpu().numpy()[s == 0])
+    assert (got == want).all()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_caller_owned_workspace(kind):
+    q = gq.Queue(kind, 1 << 10, 8, 1024, use_torch_memory=True)
+    assert gq.gq_info(q.handle)[1] is False
+    items = torch.arange(100, dtype=torch.int64, device=DEV)
+    q.enqueue(items)
+    out = torch.zeros(100, dtype=torch.int64, device=DEV)
+    ok = torch.zeros(1, dtype=torch.int64, device=DEV)
+    q.dequeue(out, None, ok)
+    assert q.sync_status() == 0
+    assert int(ok.item()) == 100
+    assert sorted(out.cpu().tolist()) == list(range(100))
+    q.reset()
+    q.dequeue(out, None, ok)
+    assert q.sync_status() == 0 and int(ok.item()) == 0

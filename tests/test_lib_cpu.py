@@ -1,0 +1,85 @@
+"""libgq loads and exports every symbol its headers declare; host-side argument
+validation and workspace layout need no GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2606_01693_gb300 as gq
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for h in ("gq.h", "gq_drivers.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:int|const char\*|void)\s+(gq_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_exports_every_declared_symbol():
+    L = gq.load()
+    declared = _declared_symbols()
+    assert declared, "no declarations parsed"
+    assert declared == set(gq.EXPORTS)
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_status_strings():
+    assert gq.status_str(0) == "ok"
+    assert gq.status_str(gq.GQ_ERR_TIMEOUT) == "bounded device loop expired"
+
+
+@pytest.mark.parametrize("kind,cap,elem,thr", [
+    (gq.GQ_LFQ, 3, 8, 1),         # capacity not a power of two
+    (gq.GQ_LFQ, 1, 8, 1),         # capacity < 2
+    (gq.GQ_LFQ, 1 << 32, 8, 1),   # above the 32-bit index field
+    (gq.GQ_WFQ, 1 << 24, 8, 1),   # above the 24-bit index field
+    (gq.GQ_LFQ, 16, 2, 1),        # element size
+    (gq.GQ_YMC, 1, 8, 1),         # pool too small
+    (7, 16, 8, 1),                # kind
+    (gq.GQ_LFQ, 16, 8, 0),        # no threads
+])
+def test_invalid_arguments_rejected(kind, cap, elem, thr):
+    with pytest.raises(gq.GqError) as ei:
+        gq.gq_workspace_bytes(kind, cap, elem, thr)
+    assert ei.value.status == gq.GQ_ERR_INVALID
+    h = ctypes.c_void_p(0)
+    assert gq.load().gq_create(kind, cap, elem, thr, None, None, None, ctypes.byref(h)) == gq.GQ_ERR_INVALID
+    assert not h.value
+
+
+def test_wfq_cycle_soundness_bound():
+    # Lemma "Modular cycle correctness": sound iff R > D k / n + 6.
+    # R = 2^4 = 16, D = 64, n = 64: k = 9 gives 9 + 6 = 15 < 16 (ok), k = 10 gives 16 (rejected).
+    ok = gq.gq_options(cycle_bits=4, help_delay=64)
+    assert gq.gq_workspace_bytes(gq.GQ_WFQ, 64, 8, 9, ok) > 0
+    with pytest.raises(gq.GqError) as ei:
+        gq.gq_workspace_bytes(gq.GQ_WFQ, 64, 8, 10, ok)
+    assert ei.value.status == gq.GQ_ERR_TOO_MANY_THREADS
+
+
+def test_bad_options_rejected():
+    for o in (gq.gq_options(batch_width=3), gq.gq_options(batch_width=64), gq.gq_options(cycle_bits=32),
+              gq.gq_options(start_ticket=5)):
+        with pytest.raises(gq.GqError):
+            gq.gq_workspace_bytes(gq.GQ_LFQ, 16, 8, 1, o)
+
+
+def test_workspace_grows_with_capacity_and_records():
+    a = gq.gq_workspace_bytes(gq.GQ_LFQ, 1 << 10, 8, 1)
+    b = gq.gq_workspace_bytes(gq.GQ_LFQ, 1 << 20, 8, 1)
+    # 2 rings x 2n slots x 8 B + n payloads x 8 B
+    assert b - a == (2 * 2 * 8 + 8) * ((1 << 20) - (1 << 10))
+    w1 = gq.gq_workspace_bytes(gq.GQ_WFQ, 1 << 10, 8, 1024)
+    w2 = gq.gq_workspace_bytes(gq.GQ_WFQ, 1 << 10, 8, 2048)
+    assert w2 - w1 == 2 * 1024 * 128          # one 128-byte record per thread per ring
+    y = gq.gq_workspace_bytes(gq.GQ_YMC, 1000, 8, 256)
+    assert y >= 3 * 1001 * 8 + 256 * 128
+    for v in (a, b, w1, w2, y):
+        assert v % 256 == 0
