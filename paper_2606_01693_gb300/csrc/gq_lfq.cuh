@@ -87,7 +87,7 @@ __device__ int lfq_ring_enq(const gq_ring_view& r, const RingGeom& g, u32 idx, u
         u64* slot = r.slots + (t & g.smask);
         const u64 c = (t >> g.order) & g.cmask;
         u64 e = ld_acq(slot);
-        for (;;) {
+        for (; it < kRetryLimit; ++it) {
             if (!cyc_older(lfq_cycle(e), c, g) || lfq_index(e) < kBotC) break;
             if (!(e & kSafe)) {
                 // an unsafe slot may be reused only if no dequeuer has passed t
@@ -116,7 +116,7 @@ __device__ int lfq_ring_deq(const gq_ring_view& r, const RingGeom& g, u32* idx, 
         u64* slot = r.slots + (h & g.smask);
         const u64 c = (h >> g.order) & g.cmask;
         u64 e = ld_acq(slot);
-        for (;;) {
+        for (; it < kRetryLimit; ++it) {
             const u64 ec = lfq_cycle(e);
             if (ec == c) {
                 if (lfq_index(e) < kBotC) {          // Consume and return the index
@@ -164,6 +164,10 @@ __device__ int lfq_enqueue(const gq_dev& q, T v) {
     int s = lfq_ring_deq<MATCH>(q.fq, g, &i, q.err);
     if (s == GQ_EMPTY) return GQ_FULL;
     if (s != GQ_OK) return s;
+    if (i >= q.capacity) {                            // never expected: a corrupt ring entry
+        latch_error(q.err, GQ_ERR_INVALID);
+        return GQ_ERR_INVALID;
+    }
     data_store<T>(q, i, v);                           // ordered before the release CAS in aq
     return lfq_ring_enq<MATCH>(q.aq, g, i, q.err);
 }
@@ -174,6 +178,10 @@ __device__ int lfq_dequeue(const gq_dev& q, T* v) {
     u32 i;
     int s = lfq_ring_deq<MATCH>(q.aq, g, &i, q.err);
     if (s != GQ_OK) return s;
+    if (i >= q.capacity) {                            // never expected: a corrupt ring entry
+        latch_error(q.err, GQ_ERR_INVALID);
+        return GQ_ERR_INVALID;
+    }
     *v = data_load<T>(q, i);                          // after the acquire on the aq slot
     s = lfq_ring_enq<MATCH>(q.fq, g, i, q.err);       // release: the read precedes reuse
     return s == GQ_OK ? GQ_OK : s;

