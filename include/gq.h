@@ -169,6 +169,16 @@ int gq_sync_status(gq_handle h, void* stream);
 /* Copies the POD device view (for user kernels using gq_device.cuh). */
 int gq_device_view(gq_handle h, gq_dev* out);
 
+/* Rare-path event counters of a queue since its last reset (G-WFQ slow path):
+ * requests published on the slow path, peer requests helped, and failed CAS
+ * attempts on a Global word in SlowFAA.  Synchronous device-to-host copy. */
+typedef struct {
+    unsigned long long slow_requests;
+    unsigned long long helps;
+    unsigned long long global_cas_failures;
+} gq_stats;
+int gq_get_stats(gq_handle h, gq_stats* out);
+
 /* Workspace size and whether the library owns it. */
 int gq_info(gq_handle h, uint64_t* workspace_bytes, int* library_owned);
 

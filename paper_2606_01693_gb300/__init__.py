@@ -21,7 +21,7 @@ from . import build as _build
 GQ_LFQ, GQ_WFQ, GQ_YMC = 0, 1, 2
 KINDS = {"lfq": GQ_LFQ, "wfq": GQ_WFQ, "ymc": GQ_YMC}
 # queue kinds whose device code is complete
-READY_KINDS = ["lfq"]
+READY_KINDS = ["lfq", "wfq"]
 GQ_OK, GQ_FULL, GQ_EMPTY = 0, 1, 2
 GQ_ERR_INVALID, GQ_ERR_NOMEM, GQ_ERR_CUDA, GQ_ERR_TIMEOUT = -1, -2, -3, -4
 GQ_ERR_POOL_EXHAUSTED, GQ_ERR_TOO_MANY_THREADS, GQ_ERR_RESERVED_VALUE = -5, -6, -7
@@ -33,7 +33,7 @@ GQ_PEAK_SAME_ADDR_FAA, GQ_PEAK_COALESCED_CAS, GQ_PEAK_SCATTERED_CAS, GQ_PEAK_COA
 # Every symbol the headers in include/ declare.
 EXPORTS = [
     "gq_workspace_bytes", "gq_create", "gq_destroy", "gq_reset", "gq_enqueue_batch", "gq_dequeue_batch",
-    "gq_sync_status", "gq_device_view", "gq_info", "gq_status_str",
+    "gq_sync_status", "gq_device_view", "gq_info", "gq_status_str", "gq_get_stats",
     "gq_run", "gq_run_sequence", "gq_drain", "gq_atomic_peak",
 ]
 
@@ -85,6 +85,7 @@ def load() -> ctypes.CDLL:
         "gq_device_view": [P, P],
         "gq_info": [P, P, P],
         "gq_status_str": [i32],
+        "gq_get_stats": [P, P],
         "gq_run": [P, P, P],
         "gq_run_sequence": [P, P, P, u64, P, P, P],
         "gq_drain": [P, P, u64, P, P],
@@ -167,6 +168,17 @@ def gq_sync_status(h: int, stream=None) -> int:
     return load().gq_sync_status(h, _stream(stream))
 
 
+class gq_stats(ctypes.Structure):
+    _fields_ = [("slow_requests", ctypes.c_uint64), ("helps", ctypes.c_uint64),
+                ("global_cas_failures", ctypes.c_uint64)]
+
+
+def gq_get_stats(h: int) -> dict:
+    s = gq_stats()
+    _check(load().gq_get_stats(h, ctypes.byref(s)), "gq_get_stats")
+    return {f: getattr(s, f) for f, _ in gq_stats._fields_}
+
+
 def gq_info(h: int) -> tuple[int, bool]:
     b, o = ctypes.c_uint64(0), ctypes.c_int(0)
     _check(load().gq_info(h, ctypes.byref(b), ctypes.byref(o)), "gq_info")
@@ -230,6 +242,9 @@ class Queue:
 
     def dequeue(self, out, status=None, num_ok=None, stream=None):
         gq_dequeue_batch(self.handle, out, None, status, num_ok, stream)
+
+    def stats(self) -> dict:
+        return gq_get_stats(self.handle)
 
     def sync_status(self, stream=None) -> int:
         return gq_sync_status(self.handle, stream)

@@ -51,7 +51,7 @@ int resolve(int kind, uint64_t cap, uint32_t elem, uint32_t max_threads, const g
             if (!o.patience_set) { o.patience_enq = 16; o.patience_deq = 64; }
             if (o.help_delay == 0) o.help_delay = 64;
             if (max_threads > (1u << 21) - 2) return GQ_ERR_TOO_MANY_THREADS;
-            if (o.start_ticket + (4ull << 40) >= (1ull << 43)) return GQ_ERR_INVALID;
+            if (o.start_ticket >= (1ull << 43)) return GQ_ERR_INVALID;   // 43-bit Counter field
             // Lemma "Modular cycle correctness": sound iff R > D k / n + 6
             const double R = (double)(1ull << o.cycle_bits);
             if (!(R > (double)o.help_delay * (double)max_threads / (double)cap + 6.0))
@@ -397,6 +397,16 @@ extern "C" int gq_sync_status(gq_handle h, void* stream) {
         if (cudaMemcpy(h->dev.err, &z, 4, cudaMemcpyHostToDevice) != cudaSuccess) return GQ_ERR_CUDA;
         return -(int)e;
     }
+    return GQ_OK;
+}
+
+extern "C" int gq_get_stats(gq_handle h, gq_stats* out) {
+    if (!h || !out) return GQ_ERR_INVALID;
+    unsigned long long w[4] = {0, 0, 0, 0};
+    if (cudaMemcpy(w, h->dev.scratch, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return GQ_ERR_CUDA;
+    out->slow_requests = w[1];
+    out->helps = w[2];
+    out->global_cas_failures = w[3];
     return GQ_OK;
 }
 

@@ -103,9 +103,14 @@ __device__ __forceinline__ void latch_error(unsigned int* err, int code) {
     if (err) atomicCAS(err, 0u, (unsigned int)(-code));
 }
 
-// Sum of a per-thread value over the full warp, added to *dst by lane 0.
-// Must be called by all 32 lanes (kernels call it once, at their end).
+// Sum of a per-thread value over the warp, added to *dst by one lane.  Kernels
+// call it once, at their end, from every thread of the block; a partial last
+// warp (block size not a multiple of 32) falls back to one atomic per lane.
 __device__ __forceinline__ void warp_add_full(unsigned long long* dst, u64 v) {
+    if (__activemask() != 0xffffffffu) {
+        if (v) atomicAdd(dst, v);
+        return;
+    }
     __syncwarp();
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane_id() == 0 && v) atomicAdd(dst, v);

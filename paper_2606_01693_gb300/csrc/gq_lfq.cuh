@@ -68,6 +68,15 @@ __device__ __forceinline__ u64 lfq_cycle(u64 e) { return e >> 33; }
 __device__ __forceinline__ u32 lfq_index(u64 e) { return (u32)e; }
 __device__ __forceinline__ u64 lfq_entry(u64 cyc, u64 safe, u32 idx) { return (cyc << 33) | safe | idx; }
 
+// Threshold updates are relaxed RMWs: the counter carries no payload, and an
+// RMW is performed at L2 before the issuing thread continues, so a later
+// operation (in real time) reads the updated value.  The reset's old value is
+// consumed so that it is issued as a returning atomic, not a fire-and-forget.
+__device__ __forceinline__ void thr_reset(i64* thr, i64 v, unsigned int* err) {
+    if (aref<i64>(*thr).exchange(v, kRlx) == INT64_MIN) latch_error(err, GQ_ERR_INVALID);
+}
+__device__ __forceinline__ i64 thr_dec(i64* thr) { return aref<i64>(*thr).fetch_add(-1, kRlx); }
+
 // Catch Tail up to at least `head` (Algorithm 1 TryDeq, "catch up Tail").
 __device__ __forceinline__ void ring_catchup(const gq_ring_view& r, u64 tail, u64 head) {
     for (u32 it = 0; it < kRetryLimit; ++it) {
@@ -94,9 +103,7 @@ __device__ int lfq_ring_enq(const gq_ring_view& r, const RingGeom& g, u32 idx, u
                 if ((i64)(ld_rlx(r.head) - t) > 0) break;
             }
             if (cas(slot, e, lfq_entry(c, kSafe, idx))) {
-                if (ld_rlx(r.threshold) != g.thr_reset) {
-                    if (exch(r.threshold, g.thr_reset) == INT64_MIN) latch_error(err, GQ_ERR_INVALID);
-                }
+                if (ld_rlx(r.threshold) != g.thr_reset) thr_reset(r.threshold, g.thr_reset, err);
                 return GQ_OK;
             }
             // CAS lost: e holds the current entry; re-evaluate the same ticket
@@ -120,7 +127,8 @@ __device__ int lfq_ring_deq(const gq_ring_view& r, const RingGeom& g, u32* idx, 
             const u64 ec = lfq_cycle(e);
             if (ec == c) {
                 if (lfq_index(e) < kBotC) {          // Consume and return the index
-                    const u64 before = fetch_or(slot, kBotC);
+                    // relaxed: the acquire load of e already ordered the payload read
+                    const u64 before = aref<u64>(*slot).fetch_or(kBotC, kRlx);
                     *idx = lfq_index(before);
                     return GQ_OK;
                 }
@@ -136,10 +144,10 @@ __device__ int lfq_ring_deq(const gq_ring_view& r, const RingGeom& g, u32* idx, 
         const u64 tl = ld_rlx(r.tail);
         if ((i64)(tl - (h + 1)) <= 0) {
             ring_catchup(r, tl, h + 1);
-            faa(r.threshold, -1);
+            thr_dec(r.threshold);
             return GQ_EMPTY;
         }
-        if (faa(r.threshold, -1) <= 0) return GQ_EMPTY;
+        if (thr_dec(r.threshold) <= 0) return GQ_EMPTY;
     }
     latch_error(err, GQ_ERR_TIMEOUT);
     return GQ_ERR_TIMEOUT;

@@ -1,12 +1,47 @@
-// G-WFQ (Section III-C).  Placeholder until the slow path lands; the word
-// layouts below are final.
+// G-WFQ: bounded wait-free ring (Section III-C, Algorithm 2).
+//
+// Same bounded 2n-slot ring and index-indirection layer as G-LFQ; the fast
+// path is G-LFQ's (Algorithm 1) and runs at most `patience` times.  After that
+// the operation publishes a request in its fixed per-thread record and every
+// thread that sees the request (the owner itself, and peers that inspect one
+// record every D operations) runs the same cooperative slow path until the
+// request's FIN bit is set.  Every shared word is updated by one 64-bit atomic
+// (Lemma "Single-word shared-state atomicity"):
+//
+//   slot   <Note 19 | Cycle 19 | Safe 1 | Enq 1 | Index 24>
+//   Global Head / Tail  <Counter 43 | ThrIdx 21>   ThrIdx 0 = NULL, else helper h + 1
+//   Local  head / tail  <Counter 62 | INC 1 | FIN 1>  (Counter holds a 43-bit ticket)
+//   phase-2 word of helper h, one per side   <request record r + 1 (21) | Counter 43>
+//
+// SlowFAA (Algorithm 2) gives all helpers of request r one agreed sequence of
+// tickets, each reserved by exactly one CAS on Global <c, NULL> -> <c + 1, h>
+// (Lemma "One cooperative increment per round"): a helper first proposes c in
+// r's local word with INC set, publishes its phase-2 word (r, c), then CASes
+// Global.  Whoever later reads ThrIdx = h completes the phase-2 step: clears
+// INC on r's local word (the ticket is now r's) and then clears ThrIdx.
+//
+// TryEnqSlow installs the entry with Enq = 0; the request finishes when FIN is
+// set on its local tail at the installed ticket; the Enq bit then goes to 1.
+// A dequeuer that meets an Enq = 0 entry of its own cycle finishes that
+// request first (FIN, then Enq = 1) and only then consumes it, so an entry is
+// never consumed while helpers could still move its request to a new ticket.
+// A slow helper that finds an old-cycle slot unusable for the request's ticket
+// advances Note to the ticket's cycle before giving up on it, so a delayed
+// helper of the same request can never install at that ticket later (Lemma
+// "Stale-slot exclusion").  A slow dequeue only locates the outcome (the
+// ticket whose slot holds an item, or an EMPTY decision) and sets FIN there;
+// the owner consumes the item, so exactly one consume happens.
+//
+// Helpers accept a request only if its published sequence fields match
+// (seq2 == seq1 with the pending bit set, Section III-C "GPU publication
+// discipline") and stop as soon as the owner's seq1 moves on.
 #pragma once
+
 #include "gq_lfq.cuh"
+
 namespace gqd {
 
-// Slot <Note 19 | Cycle 19 | Safe 1 | Enq 1 | Index 24> (Fig. "Entry word for
-// G-WFQ", widths as read for this build: the 8-bit tags of the figure are too
-// narrow for R > Dk/n + 6 at k > n).
+// ---- word layouts --------------------------------------------------------
 constexpr int kWNoteShift = 45, kWCycShift = 26;
 constexpr u64 kWSafe = 1ull << 25, kWEnq = 1ull << 24;
 constexpr u32 kWIdxMask = (1u << 24) - 1;
@@ -16,15 +51,487 @@ constexpr u64 kWFieldMask = (1ull << 19) - 1;
 __host__ __device__ __forceinline__ u64 wfq_entry(u64 note, u64 cyc, u64 safe, u64 enq, u32 idx) {
     return (note << kWNoteShift) | (cyc << kWCycShift) | (safe ? kWSafe : 0) | (enq ? kWEnq : 0) | idx;
 }
+__device__ __forceinline__ u64 w_note(u64 e) { return (e >> kWNoteShift) & kWFieldMask; }
+__device__ __forceinline__ u64 w_cyc(u64 e) { return (e >> kWCycShift) & kWFieldMask; }
+__device__ __forceinline__ u32 w_idx(u64 e) { return (u32)e & kWIdxMask; }
+__device__ __forceinline__ u64 w_set_note(u64 e, u64 note) {
+    return (e & ~(kWFieldMask << kWNoteShift)) | (note << kWNoteShift);
+}
 
-// Global Head/Tail <Counter 43 | ThrIdx 21>, ThrIdx 0 = NULL, record r -> r + 1.
 constexpr int kGThrBits = 21;
 constexpr u64 kGThrMask = (1ull << kGThrBits) - 1;
 constexpr u64 kGOne = 1ull << kGThrBits;
+constexpr u64 kCntMask = (1ull << 43) - 1;
 __host__ __device__ __forceinline__ u64 wfq_global(u64 cnt, u64 thr) { return (cnt << kGThrBits) | thr; }
+__device__ __forceinline__ u64 g_cnt(u64 g) { return g >> kGThrBits; }
+__device__ __forceinline__ u64 g_thr(u64 g) { return g & kGThrMask; }
+
+constexpr u64 kLInc = 2, kLFin = 1;
+__device__ __forceinline__ u64 l_cnt(u64 l) { return (l >> 2) & kCntMask; }
+
+// 43-bit modular ticket order (sound while live tickets are within 2^42)
+__device__ __forceinline__ bool cnt_lt(u64 a, u64 b) {
+    const u64 d = (b - a) & kCntMask;
+    return d != 0 && d < (1ull << 42);
+}
+__device__ __forceinline__ bool cnt_le(u64 a, u64 b) { return a == b || cnt_lt(a, b); }
+
+// ---- per-thread record (128 bytes) ----------------------------------------
+enum : int {
+    kRSeq1 = 0,      // owner: number of finished slow requests
+    kRSeq2 = 1,      // published request sequence
+    kRPending = 2,   // bit0 pending, bit1 enqueue
+    kRInit = 3,      // initial ticket
+    kRLocalTail = 4, // <Counter, INC, FIN> of an enqueue request
+    kRLocalHead = 5, // <Counter, INC, FIN> of a dequeue request
+    kRIndex = 6,     // payload index of an enqueue request
+    kRP2Tail = 7,    // this thread's phase-2 word as a helper on Tail
+    kRP2Head = 8,    // ... on Head
+    kRPrivate = 9,   // owner only: help countdown (low 32) | next peer (high 32)
+    kRWords = 16
+};
+
+// Retry budget of the cooperative slow path.  Its CAS on the Global word can
+// lose to fast-path fetch-adds for as long as fast traffic lasts (Algorithm 2
+// assumes that traffic subsides as threads turn to helping), so the budget is
+// larger than the fast path's; it is one budget for all rounds of one
+// request by one helper.  Reaching it latches GQ_ERR_TIMEOUT.
+constexpr u32 kSlowLimit = 1u << 18;
+
+// Rare-path event counters kept in the queue's scratch line.
+enum { kStatSlowRequests = 1, kStatHelps = 2, kStatGlobalCasFail = 3 };
+
+struct WfqCtx {
+    RingGeom g;
+    u64 cmask, half;
+    u32 k;           // records
+    u32 help_delay;
+    u64 n;           // capacity (index bound)
+    unsigned int* err;
+    unsigned long long* stats;
+};
+
+__device__ __forceinline__ bool wc_older(u64 a, u64 b, const WfqCtx& x) {
+    const u64 d = (b - a) & x.cmask;
+    return d != 0 && d < x.half;
+}
+// newest of two notes (modular); used to keep Note within one cycle of the slot
+__device__ __forceinline__ u64 note_fresh(u64 note, u64 c, const WfqCtx& x) {
+    const u64 cm1 = (c - 1) & x.cmask;
+    return wc_older(note, cm1, x) ? cm1 : note;
+}
+
+__device__ __forceinline__ u64* rec_of(const gq_ring_view& r, u32 id) { return r.rec + (u64)id * kRWords; }
+
+// ---- phase 2 (Algorithm 2: "help the phase-2 request named by u") ----------
+// g names helper h; h's phase-2 word (r, c) belongs to the instance named by g
+// only if c < Counter(g) (a newer instance of h has c >= Counter(g)).
+__device__ __forceinline__ void help_phase2(const gq_ring_view& R, int side, u64* G, u64 g) {
+    const u32 h = (u32)g_thr(g) - 1;
+    const u64 p = ld_acq(rec_of(R, h) + (side ? kRP2Head : kRP2Tail));
+    const u64 rr = p >> 43;
+    const u64 c = p & kCntMask;
+    if (rr != 0 && cnt_lt(c, g_cnt(g))) {
+        u64 want = (c << 2) | kLInc;
+        cas(rec_of(R, (u32)rr - 1) + (side ? kRLocalHead : kRLocalTail), want, c << 2);
+    }
+    u64 gg = g;
+    cas(G, gg, g & ~kGThrMask);
+}
+
+// Request validity: the owner's seq1 has not moved past `seq`.
+__device__ __forceinline__ bool req_live(const gq_ring_view& R, u32 r, u64 seq) {
+    return ld_acq(rec_of(R, r) + kRSeq1) == seq;
+}
+
+// SlowFAA (Algorithm 2).  Obtains the next ticket of request r (owner's
+// sequence `seq`) on `side` (0 tail, 1 head).  *v: the last ticket this helper
+// tried for r; on true it holds the new ticket.  Returns false when the request
+// is finished (FIN) or no longer live.
+static __device__ __noinline__ bool slow_faa(const gq_ring_view& R, int side, u32 r, u64 seq, u32 me, u64* v, i64* thld,
+                         const WfqCtx& x, u32* budget) {
+    u64* G = side ? R.head : R.tail;
+    u64* L = rec_of(R, r) + (side ? kRLocalHead : kRLocalTail);
+    u64* P2 = rec_of(R, me) + (side ? kRP2Head : kRP2Tail);
+    while (*budget) {
+        --*budget;
+        const u64 g = ld_acq(G);
+        if (g_thr(g) != 0) {
+            help_phase2(R, side, G, g);
+            continue;
+        }
+        u64 l = ld_acq(L);
+        if ((l & kLFin) || !req_live(R, r, seq)) return false;
+        const u64 c = g_cnt(g);
+        u64 lc = l_cnt(l);
+        if (!(l & kLInc)) {
+            if (lc != *v) {               // another helper already moved r to a new ticket
+                *v = lc;
+                return true;
+            }
+            const u64 prop = (c << 2) | kLInc;   // r's ticket *v failed: propose c
+            if (!cas(L, l, prop)) continue;
+            l = prop;
+            lc = c;
+        }
+        if (lc != c) {
+            // G was read with ThrIdx NULL before L: a proposal older than c was
+            // never reserved (its reservation would have cleared INC first)
+            if (cnt_lt(lc, c)) cas(L, l, (c << 2) | kLInc);
+            continue;
+        }
+        st_rel(P2, ((u64)(r + 1) << 43) | c);
+        u64 gg = g;
+        if (cas(G, gg, wfq_global(c + 1, me + 1))) {
+            if (thld) thr_dec(thld);
+            u64 want = (c << 2) | kLInc;
+            cas(L, want, c << 2);
+            for (; *budget; --*budget) {              // clear ThrIdx if it is still ours
+                u64 cur = ld_acq(G);
+                if (g_thr(cur) != me + 1) break;
+                if (cas(G, cur, cur & ~kGThrMask)) break;
+            }
+            *v = c;
+            return true;
+        }
+        if (x.stats) atomicAdd(x.stats + kStatGlobalCasFail, 1ull);
+    }
+    latch_error(x.err, GQ_ERR_TIMEOUT);
+    return false;
+}
+
+// Catch the Global Tail counter up to at least `head` (keeps ThrIdx).
+__device__ __forceinline__ void wfq_catchup(const gq_ring_view& R, u64 head) {
+    u64 g = ld_acq(R.tail);
+    for (u32 it = 0; it < kRetryLimit; ++it) {
+        if (cnt_le(head, g_cnt(g))) return;
+        if (cas(R.tail, g, wfq_global(head, g_thr(g)))) return;
+    }
+}
+
+// Finishes the slow enqueue that installed entry e (Enq = 0) at ticket t:
+// FIN on its request at t (owner looked up by index), then Enq = 1.
+static __device__ __noinline__ void wfq_finalize(const gq_ring_view& R, u64* slot, u64 e, u64 t, const WfqCtx& x) {
+    const u32 i = w_idx(e);
+    if (i >= x.n) {
+        latch_error(x.err, GQ_ERR_INVALID);
+        return;
+    }
+    const u64 o = ld_acq(R.owner + i);
+    if (o != 0 && o <= x.k) {
+        u64 want = t << 2;
+        cas(rec_of(R, (u32)o - 1) + kRLocalTail, want, want | kLFin);
+    }
+    const u64 c = w_cyc(e);
+    for (u32 it = 0; it < kRetryLimit; ++it) {
+        if (w_cyc(e) != c || w_idx(e) != i || (e & kWEnq)) return;
+        if (cas(slot, e, e | kWEnq)) return;
+    }
+}
+
+// ---- fast path (Algorithm 1 on the G-WFQ entry) ----------------------------
+enum { kTryOk = 0, kTryEmpty = 2, kTryRetry = 3 };
+
+template <bool MATCH>
+__device__ int wfq_try_enq(const gq_ring_view& R, const WfqCtx& x, u32 idx, u64* t_out) {
+    const u64 t = warp_faa<MATCH>(R.tail, kGOne, x.g.width) >> kGThrBits & kCntMask;
+    *t_out = t;
+    u64* slot = R.slots + (t & x.g.smask);
+    const u64 c = (t >> x.g.order) & x.cmask;
+    u64 e = ld_acq(slot);
+    for (u32 it = 0; it < kRetryLimit; ++it) {
+        if (!wc_older(w_cyc(e), c, x) || w_idx(e) < kWBotC) break;
+        if (!(e & kWSafe) && !cnt_le(g_cnt(ld_rlx(R.head)), t)) break;
+        if (cas(slot, e, wfq_entry(note_fresh(w_note(e), c, x), c, 1, 1, idx))) {
+            if (ld_rlx(R.threshold) != x.g.thr_reset) thr_reset(R.threshold, x.g.thr_reset, x.err);
+            return kTryOk;
+        }
+    }
+    return kTryRetry;
+}
+
+// Consumes the item of ticket h in `slot` (its cycle already checked).
+__device__ __forceinline__ u32 wfq_consume(const gq_ring_view& R, u64* slot, u64 e, u64 h, const WfqCtx& x) {
+    if (!(e & kWEnq)) wfq_finalize(R, slot, e, h, x);
+    return w_idx(aref<u64>(*slot).fetch_or(kWBotC, kRlx));   // e was read with acquire
+}
+
+template <bool MATCH>
+__device__ int wfq_try_deq(const gq_ring_view& R, const WfqCtx& x, u32* idx, u64* h_out) {
+    const u64 h = warp_faa<MATCH>(R.head, kGOne, x.g.width) >> kGThrBits & kCntMask;
+    *h_out = h;
+    u64* slot = R.slots + (h & x.g.smask);
+    const u64 c = (h >> x.g.order) & x.cmask;
+    u64 e = ld_acq(slot);
+    for (u32 it = 0; it < kRetryLimit; ++it) {
+        const u64 ec = w_cyc(e);
+        if (ec == c) {
+            if (w_idx(e) < kWBotC) {
+                *idx = wfq_consume(R, slot, e, h, x);
+                return kTryOk;
+            }
+            break;
+        }
+        if (!wc_older(ec, c, x)) break;
+        const u64 ne = (w_idx(e) >= kWBotC)
+                           ? wfq_entry(note_fresh(w_note(e), c, x), c, e & kWSafe, 1, kWBot)
+                           : (e & ~kWSafe);
+        if (cas(slot, e, ne)) break;
+        if (it + 1 == kRetryLimit) {
+            latch_error(x.err, GQ_ERR_TIMEOUT);
+            return kTryRetry;
+        }
+    }
+    const u64 tl = g_cnt(ld_rlx(R.tail));
+    if (cnt_le(tl, h + 1)) {
+        wfq_catchup(R, h + 1);
+        thr_dec(R.threshold);
+        return kTryEmpty;
+    }
+    if (thr_dec(R.threshold) <= 0) return kTryEmpty;
+    return kTryRetry;
+}
+
+// ---- slow path slot actions ------------------------------------------------
+enum { kSlowDone = 0, kSlowNext = 1 };
+
+// TryEnqSlow: install idx at ticket t (Enq = 0), or rule the slot out (Note).
+static __device__ __noinline__ int wfq_try_enq_slow(const gq_ring_view& R, const WfqCtx& x, u32 r, u64 t, u32 idx) {
+    u64* slot = R.slots + (t & x.g.smask);
+    const u64 c = (t >> x.g.order) & x.cmask;
+    u64 e = ld_acq(slot);
+    for (u32 it = 0; it < kRetryLimit; ++it) {
+        const u64 ec = w_cyc(e);
+        if (ec == c) {
+            // only r holds tail ticket t: an item of cycle c here is r's install
+            if (w_idx(e) < kWBotC) {
+                u64 want = t << 2;
+                cas(rec_of(R, r) + kRLocalTail, want, want | kLFin);
+                return kSlowDone;
+            }
+            return kSlowNext;
+        }
+        if (!wc_older(ec, c, x) || !wc_older(w_note(e), c, x)) return kSlowNext;
+        const bool usable = (w_idx(e) >= kWBotC) && ((e & kWSafe) || cnt_le(g_cnt(ld_rlx(R.head)), t));
+        if (usable) {
+            if (cas(slot, e, wfq_entry(note_fresh(w_note(e), c, x), c, 1, 0, idx))) {
+                if (ld_rlx(R.threshold) != x.g.thr_reset) thr_reset(R.threshold, x.g.thr_reset, x.err);
+                u64 want = t << 2;
+                cas(rec_of(R, r) + kRLocalTail, want, want | kLFin);
+                return kSlowDone;
+            }
+        } else {
+            if (cas(slot, e, w_set_note(e, c))) return kSlowNext;   // stale-slot exclusion
+        }
+    }
+    return kSlowNext;
+}
+
+// TryDeqSlow: find the outcome of head ticket h for request r; FIN marks it.
+static __device__ __noinline__ int wfq_try_deq_slow(const gq_ring_view& R, const WfqCtx& x, u32 r, u64 h) {
+    u64* slot = R.slots + (h & x.g.smask);
+    u64* L = rec_of(R, r) + kRLocalHead;
+    const u64 c = (h >> x.g.order) & x.cmask;
+    u64 e = ld_acq(slot);
+    for (u32 it = 0; it < kRetryLimit; ++it) {
+        const u64 ec = w_cyc(e);
+        if (ec == c) {
+            if (w_idx(e) < kWBotC) {            // the item of ticket h: the owner consumes it
+                u64 want = h << 2;
+                cas(L, want, want | kLFin);
+                return kSlowDone;
+            }
+            break;                               // ruled out at cycle c already
+        }
+        if (!wc_older(ec, c, x)) break;
+        u64 ne;
+        if (w_idx(e) >= kWBotC) {
+            ne = wfq_entry(note_fresh(w_note(e), c, x), c, e & kWSafe, 1, kWBot);
+        } else {
+            ne = e & ~kWSafe;
+            if (wc_older(w_note(e), c, x)) ne = w_set_note(ne, c);
+        }
+        if (cas(slot, e, ne)) break;
+        if (it + 1 == kRetryLimit) {
+            latch_error(x.err, GQ_ERR_TIMEOUT);
+            return kSlowNext;
+        }
+    }
+    const u64 tl = g_cnt(ld_rlx(R.tail));
+    if (cnt_le(tl, h + 1)) {
+        wfq_catchup(R, h + 1);
+        u64 want = h << 2;
+        cas(L, want, want | kLFin);
+        return kSlowDone;
+    }
+    if (ld_rlx(R.threshold) < 0) {
+        u64 want = h << 2;
+        cas(L, want, want | kLFin);
+        return kSlowDone;
+    }
+    return kSlowNext;
+}
+
+// Runs request r (sequence seq) to completion as one of its helpers.
+static __device__ __noinline__ void wfq_help_request(const gq_ring_view& R, const WfqCtx& x, u32 r, u64 seq, bool enq, u64 init,
+                                 u32 idx, u32 me) {
+    u64 v = init;
+    const int side = enq ? 0 : 1;
+    i64* thld = enq ? nullptr : R.threshold;
+    u32 budget = kSlowLimit;
+    while (budget) {
+        if (!slow_faa(R, side, r, seq, me, &v, thld, x, &budget)) return;
+        const int s = enq ? wfq_try_enq_slow(R, x, r, v, idx) : wfq_try_deq_slow(R, x, r, v);
+        if (s == kSlowDone) return;
+    }
+    latch_error(x.err, GQ_ERR_TIMEOUT);
+}
+
+// Every D operations inspect one peer record (round robin) and help it if a
+// request is pending with matching sequence fields.
+static __device__ __noinline__ void wfq_maybe_help(const gq_ring_view& R, const WfqCtx& x, u32 me) {
+    u64* priv = rec_of(R, me) + kRPrivate;
+    u64 pv = *priv;                       // owner-only word: plain access
+    u32 countdown = (u32)pv;
+    u32 peer = (u32)(pv >> 32);
+    if (countdown > 1 && countdown <= x.help_delay) {
+        *priv = (pv & ~0xFFFFFFFFull) | (countdown - 1);
+        return;
+    }
+    peer = (peer + 1) % x.k;
+    if (peer == me) peer = (peer + 1) % x.k;
+    *priv = ((u64)peer << 32) | x.help_delay;
+    if (peer == me) return;
+    u64* pr = rec_of(R, peer);
+    const u64 pend = ld_acq(pr + kRPending);
+    if (!(pend & 1)) return;
+    const u64 s2 = ld_acq(pr + kRSeq2);
+    const u64 init = ld_acq(pr + kRInit);
+    const u64 idx = ld_acq(pr + kRIndex);
+    const u64 pend2 = ld_acq(pr + kRPending);
+    const u64 s1 = ld_acq(pr + kRSeq1);
+    if (s1 != s2 || !(pend2 & 1)) return;
+    if (x.stats) atomicAdd(x.stats + kStatHelps, 1ull);
+    wfq_help_request(R, x, peer, s2, (pend2 & 2) != 0, init, (u32)idx, me);
+}
+
+// Publishes a request in the caller's record, helps it to completion, and
+// retires it.  Returns the final local word (FIN set) or 0 on timeout.
+static __device__ __noinline__ u64 wfq_slow_request(const gq_ring_view& R, const WfqCtx& x, u32 me, bool enq, u64 init, u32 idx) {
+    u64* rec = rec_of(R, me);
+    const u64 seq = ld_rlx(rec + kRSeq1);
+    u64* L = rec + (enq ? kRLocalTail : kRLocalHead);
+    st_rlx(rec + kRInit, init);
+    st_rlx(rec + kRIndex, idx);
+    if (enq) st_rel(R.owner + idx, me + 1);
+    st_rel(L, init << 2);
+    st_rel(rec + kRSeq2, seq);
+    st_rel(rec + kRPending, 1ull | (enq ? 2ull : 0ull));
+    if (x.stats) atomicAdd(x.stats + kStatSlowRequests, 1ull);
+    wfq_help_request(R, x, me, seq, enq, init, idx, me);
+    const u64 l = ld_acq(L);
+    st_rel(rec + kRPending, 0);
+    st_rel(rec + kRSeq1, seq + 1);
+    return (l & kLFin) ? l : 0;
+}
+
+__device__ __forceinline__ WfqCtx wfq_ctx(const gq_dev& q) {
+    WfqCtx x;
+    x.g = ring_geom(q);
+    x.cmask = (1ull << q.cycle_bits) - 1;
+    x.half = 1ull << (q.cycle_bits - 1);
+    x.k = q.max_threads;
+    x.n = q.capacity;
+    x.help_delay = q.help_delay;
+    x.err = q.err;
+    x.stats = q.scratch;
+    return x;
+}
+
+// Inner-ring enqueue of index idx by thread `me`.
+template <bool MATCH>
+__device__ int wfq_ring_enq(const gq_ring_view& R, const WfqCtx& x, u32 idx, u32 me, u32 patience) {
+    wfq_maybe_help(R, x, me);
+    u64 t = 0;
+    for (u32 p = 0; p < patience; ++p)
+        if (wfq_try_enq<MATCH>(R, x, idx, &t) == kTryOk) return GQ_OK;
+    if (patience == 0) t = (g_cnt(ld_rlx(R.tail)) - 1) & kCntMask;   // a ticket value r never held
+    const u64 l = wfq_slow_request(R, x, me, true, t, idx);
+    if (!l) return GQ_ERR_TIMEOUT;
+    // make the entry visible to fast dequeuers if no dequeuer did it yet
+    const u64 tf = l_cnt(l);
+    u64* slot = R.slots + (tf & x.g.smask);
+    const u64 c = (tf >> x.g.order) & x.cmask;
+    u64 e = ld_acq(slot);
+    for (u32 it = 0; it < kRetryLimit; ++it) {
+        if (w_cyc(e) != c || w_idx(e) != idx || (e & kWEnq)) break;
+        if (cas(slot, e, e | kWEnq)) break;
+    }
+    return GQ_OK;
+}
+
+// Inner-ring dequeue by thread `me`: GQ_OK with *idx, or GQ_EMPTY.
+template <bool MATCH>
+__device__ int wfq_ring_deq(const gq_ring_view& R, const WfqCtx& x, u32* idx, u32 me, u32 patience) {
+    if (ld_rlx(R.threshold) < 0) return GQ_EMPTY;
+    wfq_maybe_help(R, x, me);
+    u64 h = 0;
+    for (u32 p = 0; p < patience; ++p) {
+        const int s = wfq_try_deq<MATCH>(R, x, idx, &h);
+        if (s == kTryOk) return GQ_OK;
+        if (s == kTryEmpty) return GQ_EMPTY;
+    }
+    if (patience == 0) h = (g_cnt(ld_rlx(R.head)) - 1) & kCntMask;
+    const u64 l = wfq_slow_request(R, x, me, false, h, 0);
+    if (!l) return GQ_ERR_TIMEOUT;
+    // the outcome is at ticket hf: an item of its cycle there is ours to consume
+    const u64 hf = l_cnt(l);
+    u64* slot = R.slots + (hf & x.g.smask);
+    const u64 c = (hf >> x.g.order) & x.cmask;
+    const u64 e = ld_acq(slot);
+    if (w_cyc(e) == c && w_idx(e) < kWBotC) {
+        *idx = wfq_consume(R, slot, e, hf, x);
+        return GQ_OK;
+    }
+    return GQ_EMPTY;
+}
 
 template <class T, bool MATCH>
-__device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid) { return GQ_ERR_INVALID; }
+__device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid) {
+    if (tid >= q.max_threads) {
+        latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
+        return GQ_ERR_TOO_MANY_THREADS;
+    }
+    const WfqCtx x = wfq_ctx(q);
+    u32 i;
+    int s = wfq_ring_deq<MATCH>(q.fq, x, &i, tid, q.patience_deq);
+    if (s == GQ_EMPTY) return GQ_FULL;
+    if (s != GQ_OK) return s;
+    if (i >= q.capacity) {
+        latch_error(q.err, GQ_ERR_INVALID);
+        return GQ_ERR_INVALID;
+    }
+    data_store<T>(q, i, v);
+    return wfq_ring_enq<MATCH>(q.aq, x, i, tid, q.patience_enq);
+}
+
 template <class T, bool MATCH>
-__device__ int wfq_dequeue(const gq_dev& q, T* v, u32 tid) { return GQ_ERR_INVALID; }
+__device__ int wfq_dequeue(const gq_dev& q, T* v, u32 tid) {
+    if (tid >= q.max_threads) {
+        latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
+        return GQ_ERR_TOO_MANY_THREADS;
+    }
+    const WfqCtx x = wfq_ctx(q);
+    u32 i;
+    int s = wfq_ring_deq<MATCH>(q.aq, x, &i, tid, q.patience_deq);
+    if (s != GQ_OK) return s;
+    if (i >= q.capacity) {
+        latch_error(q.err, GQ_ERR_INVALID);
+        return GQ_ERR_INVALID;
+    }
+    *v = data_load<T>(q, i);
+    s = wfq_ring_enq<MATCH>(q.fq, x, i, tid, q.patience_enq);
+    return s == GQ_OK ? GQ_OK : s;
+}
+
 }  // namespace gqd

@@ -42,7 +42,9 @@ def test_sequential_bit_exact(kind, cap, cycle_bits, seed, p, elem):
     kinds, vals = _seq_ops(seed, n, cap, p)
     if elem == 4:
         vals = vals & np.uint64(0xFFFFFFFF)
-    q = make_queue(kind, cap, elem, max_threads=64, cycle_bits=cycle_bits)
+    # one record and D = 1 keep G-WFQ's soundness bound R > Dk/n + 6 within small cycle tags
+    extra = dict(max_threads=1, help_delay=1) if kind == "wfq" else dict(max_threads=64)
+    q = make_queue(kind, cap, elem, cycle_bits=cycle_bits, **extra)
     dk = torch.from_numpy(kinds).to(DEV)
     dv = torch.from_numpy(vals.view(np.int64)).to(DEV)
     ds = torch.zeros(n, dtype=torch.int8, device=DEV)

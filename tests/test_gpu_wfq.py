@@ -1,0 +1,110 @@
+"""G-WFQ slow path on the GPU against the oracle (run with -m gpu).
+
+Patience 0 sends every operation through the cooperative slow path
+(Algorithm 2: SlowFAA, TryEnqSlow / TryDeqSlow, phase-2 helping, Enq-bit
+finalisation); help delay D = 1 makes every operation inspect and help a peer
+record.  Results must still be exactly the sequential FIFO's (one thread) or
+pass the linearizability and run-log checks (many threads).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2606_01693_gb300 as gq
+import synth
+
+from gpu_util import DEV, drain, make_queue, run_log, u64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("cap,seed", [(2, 1), (4, 2), (64, 3)])
+def test_slow_path_sequential_bit_exact(cap, seed):
+    kinds, vals = synth.random_op_list(seed, 3000, 0.5)
+    q = make_queue("wfq", cap, 8, max_threads=1, help_delay=1, patience_enq=0, patience_deq=0)
+    dk = torch.from_numpy(kinds).to(DEV)
+    dv = torch.from_numpy(vals.view(np.int64)).to(DEV)
+    ds = torch.zeros(len(kinds), dtype=torch.int8, device=DEV)
+    do = torch.zeros(len(kinds), dtype=torch.int64, device=DEV)
+    gq.gq_run_sequence(q.handle, dk, dv, ds, do)
+    assert q.sync_status() == 0
+    want_s, want_o, final = oracle.seqfifo_run(cap, kinds, vals)
+    assert (ds.cpu().numpy() == want_s).all()
+    assert (u64(do) == want_o).all()
+    assert (drain(q, cap) == final).all()
+    st = q.stats()
+    # every ring operation went slow: each queue op is two ring ops
+    assert st["slow_requests"] >= len(kinds)
+
+
+@pytest.mark.parametrize("patience", [0, 1])
+@pytest.mark.parametrize("help_delay", [1, 64])
+def test_slow_path_concurrent_mixed(patience, help_delay):
+    T, K = 1 << 12, 40
+    sched = synth.mixed_schedule_bits(17, T, K)
+    q = make_queue("wfq", 1 << 10, 8, max_threads=T, help_delay=help_delay,
+                   patience_enq=patience, patience_deq=patience)
+    r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched)
+    left = drain(q, 1 << 10)
+    rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
+    assert rep["violations"] == 0, rep
+    assert r["counts"][gq.GQ_CNT_ERRORS] == 0
+    st = q.stats()
+    assert st["slow_requests"] > 0
+    if help_delay == 1 and patience == 0:
+        assert st["helps"] > 0
+
+
+@pytest.mark.parametrize("frac", [0.1, 0.9])
+def test_slow_path_split_full_and_empty(frac):
+    T, total, cap = 1 << 12, 200000, 1 << 8
+    P = int(frac * T)
+    q = make_queue("wfq", cap, 8, max_threads=T, patience_enq=0, patience_deq=0, help_delay=8)
+    r = run_log(q, gq.GQ_RUN_SPLIT, T, producers=P, total_ops=total)
+    left = drain(q, cap)
+    rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
+    assert rep["violations"] == 0, rep
+    assert rep["enq_full"] > 0 if frac == 0.9 else rep["deq_empty"] > 0
+
+
+@pytest.mark.parametrize("patience", [0, 2])
+def test_slow_path_tiny_histories(patience):
+    rng = np.random.default_rng(100 + patience)
+    for trial in range(50):
+        T = int(rng.integers(2, 7))
+        K = max(1, min(4, 24 // T))
+        sched = synth.mixed_schedule_bits(2000 + trial, T, K)
+        cap = int(rng.choice([2, 4]))
+        q = make_queue("wfq", cap, 8, max_threads=32, help_delay=1, patience_enq=patience, patience_deq=patience)
+        r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched, block=32, timestamps=True,
+                    delay_ns=int(rng.integers(0, 4000)))
+        m = r["kind"].reshape(-1) != 255
+        res = oracle.linearizable(r["kind"].reshape(-1)[m], r["val"].reshape(-1)[m], r["status"].reshape(-1)[m],
+                                  r["call"].reshape(-1)[m], r["end"].reshape(-1)[m], cap=cap)
+        assert res == 1, (trial, r)
+        q.close()
+
+
+def test_delay_injection_many_threads():
+    # delayed threads stall mid-run; helpers must finish their published requests
+    T, K = 1 << 11, 30
+    sched = synth.mixed_schedule_bits(23, T, K)
+    q = make_queue("wfq", 1 << 9, 8, max_threads=T, patience_enq=1, patience_deq=1, help_delay=2)
+    r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched, delay_ns=20000)
+    left = drain(q, 1 << 9)
+    rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
+    assert rep["violations"] == 0, rep
+
+
+def test_bulk_throughput_shape_with_slow_path_counts():
+    # the benchmark configuration: slow-path entries must stay rare with default patience
+    T, K = 1 << 18, 100
+    sched = synth.mixed_schedule_bits(0, T, K)
+    q = make_queue("wfq", 1 << 20, 8, max_threads=T)
+    r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched)
+    left = drain(q, 1 << 20)
+    rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
+    assert rep["violations"] == 0, rep
+    st = q.stats()
+    assert st["slow_requests"] < 0.01 * T * K, st
