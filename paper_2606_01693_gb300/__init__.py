@@ -21,7 +21,7 @@ from . import build as _build
 GQ_LFQ, GQ_WFQ, GQ_YMC = 0, 1, 2
 KINDS = {"lfq": GQ_LFQ, "wfq": GQ_WFQ, "ymc": GQ_YMC}
 # queue kinds whose device code is complete
-READY_KINDS = ["lfq", "wfq"]
+READY_KINDS = ["lfq", "wfq", "ymc"]
 GQ_OK, GQ_FULL, GQ_EMPTY = 0, 1, 2
 GQ_ERR_INVALID, GQ_ERR_NOMEM, GQ_ERR_CUDA, GQ_ERR_TIMEOUT = -1, -2, -3, -4
 GQ_ERR_POOL_EXHAUSTED, GQ_ERR_TOO_MANY_THREADS, GQ_ERR_RESERVED_VALUE = -5, -6, -7

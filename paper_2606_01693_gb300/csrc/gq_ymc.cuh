@@ -1,9 +1,300 @@
-// G-WFQ-YMC (Section III-A).  Placeholder until it lands.
+// G-WFQ-YMC: Yang and Mellor-Crummey's wait-free queue on a pre-allocated
+// cell pool (Section III-A).
+//
+// The queue is an infinite array of cells indexed by tickets from two
+// fetch-and-add counters, T (enqueue) and H (dequeue).  Section III-A replaces
+// the original's dynamically grown segment list and hazard-pointer reclamation
+// with a device pool and direct arithmetic lookup: the pool holds `capacity`
+// cells for tickets 1..capacity (segment s of SEG cells starts at s * SEG, so
+// cell i is simply pool[i]); running past it latches GQ_ERR_POOL_EXHAUSTED.
+// Cells are stored as three arrays (structure of arrays), one 64-bit word each:
+//   val  payload, or VBOT (2^64 - 1, never written) / VTOP (2^64 - 2, unusable)
+//   enq  0 = no request, 1 = unusable, r + 2 = enqueue request of thread r
+//   deq  0 = unclaimed, 1 = taken by a fast dequeue, r + 2 = dequeue request of r
+// Each thread owns a record (its "handle"): an enqueue request <id, val>, a
+// dequeue request <id, idx>, and the private helping cursors.
+//
+// Fast paths (at most patience + 1 attempts):
+//   enqueue: t = FAA(T); CAS val[t] VBOT -> v.
+//   dequeue: h = FAA(H); help_enq(h) settles the cell (value, unusable, or
+//            EMPTY when T <= h); a value is taken by CAS deq[h] 0 -> 1.
+// Slow paths publish the request in the record and are completed by helpers:
+//   enqueue: the owner keeps taking tickets and offering its request to cells
+//            (CAS enq[i] 0 -> r+2); a dequeuer that finds an unusable cell with
+//            a request attached claims that cell for the request (CAS id -> -i)
+//            and commits the value there.  Dequeuers also attach pending peer
+//            requests to cells they find empty (round-robin over peers).
+//   dequeue: helpers scan cells after the request's id for a candidate (a
+//            value not yet taken, or an EMPTY decision), announce it in idx and
+//            claim it with CAS deq[i] 0 -> r+2; idx = -i marks completion.
+//            After every successful dequeue a thread helps one peer's dequeue
+//            request (round-robin).
+// Warp-batched tickets (WaveFAA) serve the fast paths; the ticket order is the
+// same as with per-thread fetch-and-add (Lemma "WaveFAA preserves ticket order").
 #pragma once
+
 #include "gq_atomics.cuh"
+
 namespace gqd {
+
+constexpr u64 kVBot = ~0ull;
+constexpr u64 kVTop = ~0ull - 1;
+constexpr u64 kRefBot = 0, kRefTop = 1;
+constexpr u32 kYSpin = 16;      // reads of an empty cell before marking it unusable
+
+enum : int {
+    kYErId = 0,    // enqueue request: > 0 pending from cell id on, < 0 done at cell -id
+    kYErVal = 1,
+    kYDrId = 2,    // dequeue request: first cell
+    kYDrIdx = 3,   // > 0 announced candidate cell, < 0 done at cell -idx
+    kYEh = 4,      // private: enqueue-help peer
+    kYEi = 5,      // private: id of the peer request being helped
+    kYDh = 6,      // private: dequeue-help peer
+    kYWords = 16
+};
+
+struct YmcCtx {
+    u64* T;
+    u64* H;
+    u64* val;
+    u64* enq;
+    u64* deq;
+    u64* rec;
+    u64 cells;     // last valid cell index
+    u32 k;
+    u32 width;
+    unsigned int* err;
+};
+
+__device__ __forceinline__ u64* yrec(const YmcCtx& y, u32 r) { return y.rec + (u64)r * kYWords; }
+__device__ __forceinline__ i64 ld_i(u64* p) { return (i64)ld_acq(p); }
+
+__device__ __forceinline__ bool ycell_ok(const YmcCtx& y, u64 i) {
+    if (i >= 1 && i <= y.cells) return true;
+    latch_error(y.err, GQ_ERR_POOL_EXHAUSTED);
+    return false;
+}
+
+// Raise counter C to at least v + 1 (T or H), so that no later EMPTY decision
+// is taken below a cell that holds a committed value.
+__device__ __forceinline__ void ymc_advance(u64* C, u64 v) {
+    u64 cur = ld_acq(C);
+    for (u32 it = 0; it < kRetryLimit && cur <= v; ++it)
+        if (cas(C, cur, v + 1)) return;
+}
+
+enum { kYValue = 0, kYUnusable = 1, kYEmpty = 2 };
+
+// help_enq: settles cell i for the dequeuer `me` and returns kYValue with *v,
+// kYUnusable (try another cell), or kYEmpty (T <= i: no enqueue reached i).
+static __device__ __noinline__ int ymc_help_enq(const YmcCtx& y, u32 me, u64 i, u64* v) {
+    u64* cv = y.val + i;
+    u64* ce = y.enq + i;
+    u64 x = ld_acq(cv);
+    for (u32 s = 0; s < kYSpin && x == kVBot; ++s) x = ld_acq(cv);   // an enqueuer may be on its way
+    if (x == kVBot) {
+        if (!cas(cv, x, kVTop) && x != kVTop) { *v = x; return kYValue; }
+        x = kVTop;
+    } else if (x != kVTop) {
+        *v = x;
+        return kYValue;
+    }
+    // the cell is unusable for fast enqueues: offer it to a pending slow enqueue
+    u64 e = ld_acq(ce);
+    if (e == kRefBot) {
+        u64* mine = yrec(y, me);
+        u32 p = (u32)mine[kYEh];                   // private cursors: plain access
+        i64 s = ld_i(yrec(y, p) + kYErId);
+        if (mine[kYEi] != 0 && (i64)mine[kYEi] != s) {
+            mine[kYEi] = 0;
+            p = (p + 1) % y.k;
+            mine[kYEh] = p;
+            s = ld_i(yrec(y, p) + kYErId);
+        }
+        u64 want = kRefBot;
+        if (s > 0 && (u64)s <= i && !cas(ce, want, (u64)p + 2) && want != (u64)p + 2) {
+            mine[kYEi] = (u64)s;                   // keep helping this request
+        } else {
+            mine[kYEi] = 0;
+            mine[kYEh] = (p + 1) % y.k;
+        }
+        e = ld_acq(ce);
+        if (e == kRefBot) {
+            u64 b = kRefBot;
+            if (cas(ce, b, kRefTop)) e = kRefTop; else e = b;
+        }
+    }
+    if (e == kRefTop) return (ld_acq(y.T) <= i) ? kYEmpty : kYUnusable;
+    const u32 r = (u32)(e - 2);
+    u64* er = yrec(y, r);
+    const i64 ei = ld_i(er + kYErId);
+    const u64 ev = ld_acq(er + kYErVal);
+    if (ei > (i64)i) {
+        // the request was published after this cell; it cannot land here
+        if (ld_acq(cv) == kVTop && ld_acq(y.T) <= i) return kYEmpty;
+    } else {
+        u64 eiu = (u64)ei;
+        if ((ei > 0 && cas(er + kYErId, eiu, (u64)(-(i64)i))) || (ei == -(i64)i && ld_acq(cv) == kVTop)) {
+            ymc_advance(y.T, i);
+            st_rel(cv, ev);                        // commit the request's value in cell i
+        }
+    }
+    x = ld_acq(cv);
+    if (x == kVTop) return kYUnusable;
+    *v = x;
+    return kYValue;
+}
+
+// Slow enqueue of v by thread me whose fast path last failed at cell id.
+static __device__ __noinline__ int ymc_enq_slow(const YmcCtx& y, u32 me, u64 v, u64 id) {
+    u64* er = yrec(y, me);
+    // release: a helper that reads this value must also see the commit of this
+    // thread's previous request (its cell value), see ymc_help_enq
+    st_rel(er + kYErVal, v);
+    st_rel(er + kYErId, id);
+    u64 i = id;
+    for (u32 it = 0; it < kRetryLimit && ld_i(er + kYErId) > 0; ++it) {
+        i = faa_rlx(y.T, 1);
+        if (!ycell_ok(y, i)) {
+            // withdraw the request unless a helper has already claimed a cell
+            u64 cur = id;
+            if (cas(er + kYErId, cur, 0)) return GQ_ERR_POOL_EXHAUSTED;
+            break;
+        }
+        u64 b = kRefBot;
+        if (cas(y.enq + i, b, (u64)me + 2) && ld_acq(y.val + i) != kVTop) {
+            u64 cur = id;
+            cas(er + kYErId, cur, (u64)(-(i64)i));   // claim cell i (a helper may have claimed another)
+            break;
+        }
+    }
+    const i64 done = ld_i(er + kYErId);
+    if (done >= 0) {
+        latch_error(y.err, GQ_ERR_TIMEOUT);
+        return GQ_ERR_TIMEOUT;
+    }
+    const u64 c = (u64)(-done);
+    ymc_advance(y.T, c);
+    st_rel(y.val + c, v);
+    return GQ_OK;
+}
+
+// Helps the dequeue request of thread p (called by me).
+static __device__ __noinline__ void ymc_help_deq(const YmcCtx& y, u32 me, u32 p) {
+    u64* dr = yrec(y, p);
+    i64 idx = ld_i(dr + kYDrIdx);
+    const i64 id = ld_i(dr + kYDrId);
+    if (id <= 0 || idx < id) return;
+    i64 i = id, cand = 0, old = idx;
+    for (u32 it = 0; it < kRetryLimit; ++it) {
+        // find a candidate cell, unless one gets announced meanwhile
+        u32 jt = 0;
+        for (; jt < kRetryLimit && idx == old && cand == 0; ++jt) {
+            ++i;
+            if (!ycell_ok(y, (u64)i)) return;
+            u64 v;
+            const int s = ymc_help_enq(y, me, (u64)i, &v);
+            if (s == kYEmpty || (s == kYValue && ld_acq(y.deq + i) == kRefBot)) cand = i;
+            else idx = ld_i(dr + kYDrIdx);
+        }
+        if (jt == kRetryLimit) break;   // never claim the request's own first cell unannounced
+        if (cand != 0) {
+            u64 cur = (u64)idx;
+            if (cas(dr + kYDrIdx, cur, (u64)cand)) idx = cand;
+            else idx = (i64)cur;
+            if (idx >= cand) cand = 0;
+        }
+        if (idx < 0 || ld_i(dr + kYDrId) != id) return;    // completed
+        u64 b = kRefBot;
+        if (ld_acq(y.val + idx) == kVTop || cas(y.deq + idx, b, (u64)p + 2) || b == (u64)p + 2) {
+            u64 cur = (u64)idx;
+            cas(dr + kYDrIdx, cur, (u64)(-idx));
+            return;
+        }
+        old = idx;
+        if (idx >= i) i = idx;
+    }
+    latch_error(y.err, GQ_ERR_TIMEOUT);
+}
+
+__device__ __forceinline__ YmcCtx ymc_ctx(const gq_dev& q) {
+    YmcCtx y;
+    y.T = q.ymc_tail;
+    y.H = q.ymc_head;
+    y.val = q.cell_val;
+    y.enq = q.cell_enq;
+    y.deq = q.cell_deq;
+    y.rec = q.ymc_rec;
+    y.cells = q.capacity;
+    y.k = q.max_threads;
+    y.width = q.batch_width;
+    y.err = q.err;
+    return y;
+}
+
 template <class T, bool MATCH>
-__device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid) { return GQ_ERR_INVALID; }
+__device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid) {
+    if (tid >= q.max_threads) {
+        latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
+        return GQ_ERR_TOO_MANY_THREADS;
+    }
+    const u64 x = (u64)v;
+    if (x >= kVTop) return GQ_ERR_RESERVED_VALUE;
+    const YmcCtx y = ymc_ctx(q);
+    u64 id = 0;
+    for (u32 p = 0; p <= q.patience_enq; ++p) {
+        const u64 i = warp_faa<MATCH>(y.T, 1, y.width);
+        if (!ycell_ok(y, i)) return GQ_ERR_POOL_EXHAUSTED;
+        u64 b = kVBot;
+        if (aref<u64>(y.val[i]).compare_exchange_strong(b, x, kRel, kRlx)) return GQ_OK;
+        id = i;
+    }
+    return ymc_enq_slow(y, tid, x, id);
+}
+
 template <class T, bool MATCH>
-__device__ int ymc_dequeue(const gq_dev& q, T* v, u32 tid) { return GQ_ERR_INVALID; }
+__device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid) {
+    if (tid >= q.max_threads) {
+        latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
+        return GQ_ERR_TOO_MANY_THREADS;
+    }
+    const YmcCtx y = ymc_ctx(q);
+    u64 id = 0, v = 0;
+    int res = kYUnusable;
+    for (u32 p = 0; p <= q.patience_deq && res == kYUnusable; ++p) {
+        const u64 i = warp_faa<MATCH>(y.H, 1, y.width);
+        if (!ycell_ok(y, i)) return GQ_ERR_POOL_EXHAUSTED;
+        res = ymc_help_enq(y, tid, i, &v);
+        if (res == kYValue) {
+            u64 b = kRefBot;
+            if (!cas(y.deq + i, b, kRefTop)) res = kYUnusable;   // a slow dequeue took it
+        }
+        id = i;
+    }
+    if (res == kYUnusable) {
+        // slow path: publish <id, idx = id> and help it to completion
+        u64* dr = yrec(y, tid);
+        st_rel(dr + kYDrId, id);
+        st_rel(dr + kYDrIdx, id);
+        ymc_help_deq(y, tid, tid);
+        const i64 idx = ld_i(dr + kYDrIdx);
+        if (idx >= 0) {
+            latch_error(y.err, GQ_ERR_TIMEOUT);
+            return GQ_ERR_TIMEOUT;
+        }
+        const u64 c = (u64)(-idx);
+        ymc_advance(y.H, c);
+        v = ld_acq(y.val + c);
+        res = (v == kVTop) ? kYEmpty : kYValue;
+    }
+    if (res == kYEmpty) return GQ_EMPTY;
+    // after a successful dequeue, help one peer's dequeue request
+    u64* mine = yrec(y, tid);
+    const u32 peer = (u32)mine[kYDh];
+    mine[kYDh] = (peer + 1) % y.k;
+    if (peer != tid) ymc_help_deq(y, tid, peer);
+    *out = (T)v;
+    return GQ_OK;
+}
+
 }  // namespace gqd
