@@ -203,7 +203,11 @@ def main():
     # ---- workload ----
     sched = synth.mixed_schedule_bits(args.seed, T, K)
     dsched = torch.from_numpy(sched.view(np.int64)).to(dev)
-    queues = {k: gq.Queue(k, CAPACITY, 8, max_threads=T) for k in kinds}
+    # G-WFQ-YMC never reuses cells: its pool covers every ticket of a step
+    # (about one per operation, plus tickets burned by races), here 1.25x the
+    # operations plus 2^21 for the batch-API leg.
+    ymc_pool = int(1.25 * T * K) + (1 << 21)
+    queues = {k: gq.Queue(k, CAPACITY if k != "ymc" else ymc_pool, 8, max_threads=T) for k in kinds}
     counts = {k: torch.zeros(8, dtype=torch.int64, device=dev) for k in kinds}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     launches_per_step = {"lfq": 3, "wfq": 3, "ymc": 2}
@@ -365,7 +369,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": "pairwise 50/50 interleaved by seed, %d threads x %d ops, capacity 2^20 "
                                        "uint64, queues %s" % (T, K, "+".join(kinds)),
-                           "threads": T, "ops_per_thread": K, "capacity": CAPACITY, "block": 256, "seed": args.seed,
+                           "threads": T, "ops_per_thread": K, "capacity": CAPACITY, "ymc_pool_cells": ymc_pool,
+                           "block": 256, "seed": args.seed,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between timed steps (256 MiB write); queue state re-initialised inside "
                                  "each step"},

@@ -34,7 +34,7 @@ int resolve(int kind, uint64_t cap, uint32_t elem, uint32_t max_threads, const g
     if (!is_pow2(o.batch_width) || o.batch_width > 32) return GQ_ERR_INVALID;
     if (kind == GQ_YMC) {
         if (cap < 2 || cap > (1ull << 40)) return GQ_ERR_INVALID;
-        if (max_threads > (1u << 24)) return GQ_ERR_TOO_MANY_THREADS;
+        if (max_threads > (1u << 24) - 1) return GQ_ERR_TOO_MANY_THREADS;   // 24-bit thread field of cell references
         if (!o.patience_set) { o.patience_enq = 10; o.patience_deq = 10; }
         o.cycle_bits = 0;
         o.help_delay = 0;

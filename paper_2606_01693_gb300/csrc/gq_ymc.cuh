@@ -9,7 +9,8 @@
 // cell i is simply pool[i]); running past it latches GQ_ERR_POOL_EXHAUSTED.
 // Cells are stored as three arrays (structure of arrays), one 64-bit word each:
 //   val  payload, or VBOT (2^64 - 1, never written) / VTOP (2^64 - 2, unusable)
-//   enq  0 = no request, 1 = unusable, r + 2 = enqueue request of thread r
+//   enq  0 = no request, 1 = unusable, else (id << 24) | (r + 1): the enqueue
+//        request of thread r whose id (first failed cell) is id
 //   deq  0 = unclaimed, 1 = taken by a fast dequeue, r + 2 = dequeue request of r
 // Each thread owns a record (its "handle"): an enqueue request <id, val>, a
 // dequeue request <id, idx>, and the private helping cursors.
@@ -31,6 +32,15 @@
 //            request (round-robin).
 // Warp-batched tickets (WaveFAA) serve the fast paths; the ticket order is the
 // same as with per-thread fetch-and-add (Lemma "WaveFAA preserves ticket order").
+//
+// Difference from the CPU original: a cell's enqueue-request reference names
+// the request instance (thread and request id), not just the thread's handle.
+// Once that instance has been satisfied in another cell, the reference is
+// dead: no later request of the same thread can be claimed through this cell.
+// That makes an EMPTY decision at a cell final (its value word stays VTOP);
+// with a bare handle reference, a later request whose first failed cell lies
+// at or below this one (its ticket taken before T passed the cell) could still
+// commit a value here after a dequeuer had already answered EMPTY at it.
 #pragma once
 
 #include "gq_atomics.cuh"
@@ -67,6 +77,9 @@ struct YmcCtx {
 };
 
 __device__ __forceinline__ u64* yrec(const YmcCtx& y, u32 r) { return y.rec + (u64)r * kYWords; }
+__device__ __forceinline__ u64 ytag(u64 id, u32 r) { return (id << 24) | (u64)(r + 1); }
+__device__ __forceinline__ u32 ytag_thread(u64 e) { return (u32)(e & ((1u << 24) - 1)) - 1; }
+__device__ __forceinline__ i64 ytag_id(u64 e) { return (i64)(e >> 24); }
 __device__ __forceinline__ i64 ld_i(u64* p) { return (i64)ld_acq(p); }
 
 __device__ __forceinline__ bool ycell_ok(const YmcCtx& y, u64 i) {
@@ -112,7 +125,7 @@ static __device__ __noinline__ int ymc_help_enq(const YmcCtx& y, u32 me, u64 i, 
             s = ld_i(yrec(y, p) + kYErId);
         }
         u64 want = kRefBot;
-        if (s > 0 && (u64)s <= i && !cas(ce, want, (u64)p + 2) && want != (u64)p + 2) {
+        if (s > 0 && (u64)s <= i && !cas(ce, want, ytag((u64)s, p)) && want != ytag((u64)s, p)) {
             mine[kYEi] = (u64)s;                   // keep helping this request
         } else {
             mine[kYEi] = 0;
@@ -125,19 +138,23 @@ static __device__ __noinline__ int ymc_help_enq(const YmcCtx& y, u32 me, u64 i, 
         }
     }
     if (e == kRefTop) return (ld_acq(y.T) <= i) ? kYEmpty : kYUnusable;
-    const u32 r = (u32)(e - 2);
-    u64* er = yrec(y, r);
-    const i64 ei = ld_i(er + kYErId);
+    // the cell names request instance (id_e of thread r)
+    u64* er = yrec(y, ytag_thread(e));
+    const i64 id_e = ytag_id(e);
+    i64 ei = ld_i(er + kYErId);
     const u64 ev = ld_acq(er + kYErVal);
-    if (ei > (i64)i) {
-        // the request was published after this cell; it cannot land here
+    bool claimed = false;
+    if (ei == id_e) {
+        u64 cur = (u64)ei;
+        if (cas(er + kYErId, cur, (u64)(-(i64)i))) claimed = true;
+        else ei = (i64)cur;
+    }
+    if (claimed || (ei == -(i64)i && ld_acq(cv) == kVTop)) {
+        ymc_advance(y.T, i);
+        st_rel(cv, ev);                            // commit the request's value in cell i
+    } else if (ei != -(i64)i) {
+        // the instance was satisfied elsewhere: this cell stays unusable for good
         if (ld_acq(cv) == kVTop && ld_acq(y.T) <= i) return kYEmpty;
-    } else {
-        u64 eiu = (u64)ei;
-        if ((ei > 0 && cas(er + kYErId, eiu, (u64)(-(i64)i))) || (ei == -(i64)i && ld_acq(cv) == kVTop)) {
-            ymc_advance(y.T, i);
-            st_rel(cv, ev);                        // commit the request's value in cell i
-        }
     }
     x = ld_acq(cv);
     if (x == kVTop) return kYUnusable;
@@ -162,7 +179,7 @@ static __device__ __noinline__ int ymc_enq_slow(const YmcCtx& y, u32 me, u64 v, 
             break;
         }
         u64 b = kRefBot;
-        if (cas(y.enq + i, b, (u64)me + 2) && ld_acq(y.val + i) != kVTop) {
+        if (cas(y.enq + i, b, ytag(id, me)) && ld_acq(y.val + i) != kVTop) {
             u64 cur = id;
             cas(er + kYErId, cur, (u64)(-(i64)i));   // claim cell i (a helper may have claimed another)
             break;

@@ -106,7 +106,7 @@ def test_pairs_one_block(kind, width):
     left = drain(q, 1 << 10)
     assert len(left) == 0
     rep = oracle.check_log(r["kind"], r["status"], r["val"], left, prod_shift=16, seq_mask=0xFFFF, seq_bias=0)
-    assert rep["violations"] == 0, rep
+    assert rep["violations"] == 0, str(rep)
     assert rep["deq_ok"] == T * pairs
 
 
@@ -120,7 +120,7 @@ def test_mixed_interleaved(kind, T):
     r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched)
     left = drain(q, 1 << 20)
     rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
-    assert rep["violations"] == 0, rep
+    assert rep["violations"] == 0, str(rep)
     assert rep["enq_full"] == 0
     assert rep["enq_ok"] == int(synth.schedule_is_enq(sched, T, K).sum())
 
@@ -135,7 +135,7 @@ def test_mixed_full_size(kind):
     r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched)
     left = drain(q, 1 << 20)
     rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
-    assert rep["violations"] == 0, rep
+    assert rep["violations"] == 0, str(rep)
     c = r["counts"]
     assert c[gq.GQ_CNT_ERRORS] == 0
     assert (int(c[gq.GQ_CNT_SUM_ENQ]) - int(c[gq.GQ_CNT_SUM_DEQ]) - int(left.sum(dtype=np.uint64))) % (1 << 64) == 0
@@ -151,7 +151,7 @@ def test_split_producer_consumer(kind, frac):
     r = run_log(q, gq.GQ_RUN_SPLIT, T, producers=P, total_ops=total)
     left = drain(q, total)
     rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
-    assert rep["violations"] == 0, rep
+    assert rep["violations"] == 0, str(rep)
     assert rep["enq_ok"] + rep["enq_full"] == int(synth.split_ops_per_thread(total, T)[:P].sum())
     if ocap:
         assert len(left) <= cap

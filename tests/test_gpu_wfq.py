@@ -48,7 +48,7 @@ def test_slow_path_concurrent_mixed(patience, help_delay):
     r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched)
     left = drain(q, 1 << 10)
     rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
-    assert rep["violations"] == 0, rep
+    assert rep["violations"] == 0, str(rep)
     assert r["counts"][gq.GQ_CNT_ERRORS] == 0
     st = q.stats()
     assert st["slow_requests"] > 0
@@ -64,7 +64,7 @@ def test_slow_path_split_full_and_empty(frac):
     r = run_log(q, gq.GQ_RUN_SPLIT, T, producers=P, total_ops=total)
     left = drain(q, cap)
     rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
-    assert rep["violations"] == 0, rep
+    assert rep["violations"] == 0, str(rep)
     assert rep["enq_full"] > 0 if frac == 0.9 else rep["deq_empty"] > 0
 
 
@@ -94,7 +94,7 @@ def test_delay_injection_many_threads():
     r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched, delay_ns=20000)
     left = drain(q, 1 << 9)
     rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
-    assert rep["violations"] == 0, rep
+    assert rep["violations"] == 0, str(rep)
 
 
 def test_bulk_throughput_shape_with_slow_path_counts():
@@ -105,6 +105,6 @@ def test_bulk_throughput_shape_with_slow_path_counts():
     r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched)
     left = drain(q, 1 << 20)
     rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
-    assert rep["violations"] == 0, rep
+    assert rep["violations"] == 0, str(rep)
     st = q.stats()
     assert st["slow_requests"] < 0.01 * T * K, st

@@ -38,7 +38,7 @@ def test_concurrent_mixed_slow_and_fast(patience):
     r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched)
     left = drain(q, T * K)
     rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
-    assert rep["violations"] == 0, rep
+    assert rep["violations"] == 0, str(rep)
     assert r["counts"][gq.GQ_CNT_ERRORS] == 0
 
 
