@@ -29,8 +29,10 @@ __device__ __forceinline__ u32 mix32(u32 a, u32 b) {
     return h;
 }
 
+// 256 threads x 4 blocks per SM caps registers at 64: the rarely taken slow
+// paths of G-WFQ / G-WFQ-YMC may spill instead of halving occupancy.
 template <class T, int KIND>
-__global__ void k_run(gq_dev q, RunK a) {
+__global__ void __launch_bounds__(256, 4) k_run(gq_dev q, RunK a) {
     const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
     u64 c_enq_ok = 0, c_full = 0, c_deq_ok = 0, c_empty = 0, s_enq = 0, s_deq = 0, c_err = 0;
     if (t < a.threads) {

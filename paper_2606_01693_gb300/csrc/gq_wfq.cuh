@@ -91,12 +91,16 @@ enum : int {
     kRWords = 16
 };
 
-// Retry budget of the cooperative slow path.  Its CAS on the Global word can
-// lose to fast-path fetch-adds for as long as fast traffic lasts (Algorithm 2
-// assumes that traffic subsides as threads turn to helping), so the budget is
-// larger than the fast path's; it is one budget for all rounds of one
-// request by one helper.  Reaching it latches GQ_ERR_TIMEOUT.
-constexpr u32 kSlowLimit = 1u << 18;
+// Retry budgets of the cooperative slow path.  Its CAS on the Global word
+// loses to every other helper's winning CAS and to fast-path fetch-adds; those
+// losses are progress by others, so they do not count as stalls.  Only
+// iterations that find the Global word unchanged since the previous one count
+// against kSlowStall, and any change resets it (no thread made progress:
+// a livelock); kSlowHard caps the
+// total iterations of one request by one helper.  Reaching either latches
+// GQ_ERR_TIMEOUT.
+constexpr u32 kSlowStall = 1u << 16;
+constexpr u32 kSlowHard = 1u << 24;
 
 // Rare-path event counters kept in the queue's scratch line.
 enum { kStatSlowRequests = 1, kStatHelps = 2, kStatGlobalCasFail = 3 };
@@ -153,9 +157,13 @@ static __device__ __noinline__ bool slow_faa(const gq_ring_view& R, int side, u3
     u64* G = side ? R.head : R.tail;
     u64* L = rec_of(R, r) + (side ? kRLocalHead : kRLocalTail);
     u64* P2 = rec_of(R, me) + (side ? kRP2Head : kRP2Tail);
-    while (*budget) {
+    u64 last = ~0ull;
+    u32 stall = 0;
+    while (*budget && stall < kSlowStall) {
         --*budget;
         const u64 g = ld_acq(G);
+        stall = (g == last) ? stall + 1 : 0;
+        last = g;
         if (g_thr(g) != 0) {
             help_phase2(R, side, G, g);
             continue;
@@ -378,7 +386,7 @@ static __device__ __noinline__ void wfq_help_request(const gq_ring_view& R, cons
     u64 v = init;
     const int side = enq ? 0 : 1;
     i64* thld = enq ? nullptr : R.threshold;
-    u32 budget = kSlowLimit;
+    u32 budget = kSlowHard;
     while (budget) {
         if (!slow_faa(R, side, r, seq, me, &v, thld, x, &budget)) return;
         const int s = enq ? wfq_try_enq_slow(R, x, r, v, idx) : wfq_try_deq_slow(R, x, r, v);
