@@ -89,6 +89,7 @@ typedef struct {
     unsigned long long* slots;      /* 2n packed 64-bit entries                    */
     unsigned long long* rec;        /* G-WFQ request records (NULL for G-LFQ)      */
     unsigned long long* owner;      /* G-WFQ: record id that enqueues each index    */
+    unsigned long long* helpc;      /* G-WFQ: per-thread help cursor <peer, countdown> */
 } gq_ring_view;
 
 typedef struct {

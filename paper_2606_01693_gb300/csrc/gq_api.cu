@@ -86,6 +86,8 @@ gq_layout make_layout(int kind, uint64_t cap, uint32_t elem, uint32_t max_thread
             off = align_up(off, 256); L.fq_rec = off; off += (uint64_t)max_threads * kWfqRecBytes;
             off = align_up(off, 256); L.aq_owner = off; off += cap * 8;
             off = align_up(off, 256); L.fq_owner = off; off += cap * 8;
+            off = align_up(off, 256); L.aq_helpc = off; off += (uint64_t)max_threads * 8;
+            off = align_up(off, 256); L.fq_helpc = off; off += (uint64_t)max_threads * 8;
         }
     }
     L.total = align_up(off, 256);
@@ -266,7 +268,9 @@ extern "C" int gq_reset(gq_handle h, void* stream) {
             if (cudaMemsetAsync(d.aq.rec, 0, (uint64_t)d.max_threads * kWfqRecBytes, st) != cudaSuccess ||
                 cudaMemsetAsync(d.fq.rec, 0, (uint64_t)d.max_threads * kWfqRecBytes, st) != cudaSuccess ||
                 cudaMemsetAsync(d.aq.owner, 0, d.capacity * 8, st) != cudaSuccess ||
-                cudaMemsetAsync(d.fq.owner, 0, d.capacity * 8, st) != cudaSuccess)
+                cudaMemsetAsync(d.fq.owner, 0, d.capacity * 8, st) != cudaSuccess ||
+                cudaMemsetAsync(d.aq.helpc, 0, (uint64_t)d.max_threads * 8, st) != cudaSuccess ||
+                cudaMemsetAsync(d.fq.helpc, 0, (uint64_t)d.max_threads * 8, st) != cudaSuccess)
                 return GQ_ERR_CUDA;
         }
     }
@@ -341,6 +345,8 @@ extern "C" int gq_create(int kind, uint64_t capacity, uint32_t elem_bytes, uint3
             d.fq.rec = at<unsigned long long>(b, h->lay.fq_rec);
             d.aq.owner = at<unsigned long long>(b, h->lay.aq_owner);
             d.fq.owner = at<unsigned long long>(b, h->lay.fq_owner);
+            d.aq.helpc = at<unsigned long long>(b, h->lay.aq_helpc);
+            d.fq.helpc = at<unsigned long long>(b, h->lay.fq_helpc);
         }
     }
     s = gq_reset(h, stream);

@@ -15,7 +15,7 @@ constexpr uint64_t kLine = 128;
 struct gq_layout {
     uint64_t ctrl;       // control lines (error word, scratch, counters, thresholds)
     uint64_t aq_slots, fq_slots, data;
-    uint64_t aq_rec, fq_rec, aq_owner, fq_owner;
+    uint64_t aq_rec, fq_rec, aq_owner, fq_owner, aq_helpc, fq_helpc;
     uint64_t cell_val, cell_enq, cell_deq, ymc_rec;
     uint64_t total;
 };

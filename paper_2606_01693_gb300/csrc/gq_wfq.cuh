@@ -87,8 +87,9 @@ enum : int {
     kRIndex = 6,     // payload index of an enqueue request
     kRP2Tail = 7,    // this thread's phase-2 word as a helper on Tail
     kRP2Head = 8,    // ... on Head
-    kRPrivate = 9,   // owner only: help countdown (low 32) | next peer (high 32)
     kRWords = 16
+    // the owner-only help cursor lives in a separate compact array (helpc),
+    // so that the per-operation countdown of a warp touches one line
 };
 
 // Retry budgets of the cooperative slow path.  Its CAS on the Global word
@@ -380,35 +381,32 @@ static __device__ __noinline__ int wfq_try_deq_slow(const gq_ring_view& R, const
     return kSlowNext;
 }
 
-// Runs request r (sequence seq) to completion as one of its helpers.
-static __device__ __noinline__ void wfq_help_request(const gq_ring_view& R, const WfqCtx& x, u32 r, u64 seq, bool enq, u64 init,
-                                 u32 idx, u32 me) {
+// Runs request r (sequence seq) to completion as one of its helpers.  A slot
+// action that reports DONE has tried to set FIN at its ticket; that CAS loses
+// if another helper moved the request on first (for a dequeue, an EMPTY
+// observation at one moment and a "not empty" one at another are both valid),
+// so the loop always returns to SlowFAA, which stops only once FIN is set.
+static __device__ __noinline__ void wfq_help_request(const gq_ring_view& R, const WfqCtx& x, u32 r, u64 seq, bool enq,
+                                                     u64 init, u32 idx, u32 me) {
     u64 v = init;
     const int side = enq ? 0 : 1;
     i64* thld = enq ? nullptr : R.threshold;
     u32 budget = kSlowHard;
     while (budget) {
         if (!slow_faa(R, side, r, seq, me, &v, thld, x, &budget)) return;
-        const int s = enq ? wfq_try_enq_slow(R, x, r, v, idx) : wfq_try_deq_slow(R, x, r, v);
-        if (s == kSlowDone) return;
+        if (enq) wfq_try_enq_slow(R, x, r, v, idx);
+        else wfq_try_deq_slow(R, x, r, v);
     }
     latch_error(x.err, GQ_ERR_TIMEOUT);
 }
 
-// Every D operations inspect one peer record (round robin) and help it if a
-// request is pending with matching sequence fields.
-static __device__ __noinline__ void wfq_maybe_help(const gq_ring_view& R, const WfqCtx& x, u32 me) {
-    u64* priv = rec_of(R, me) + kRPrivate;
-    u64 pv = *priv;                       // owner-only word: plain access
-    u32 countdown = (u32)pv;
+// Inspects the next peer record (round robin) and helps it if a request is
+// pending with matching sequence fields.
+static __device__ __noinline__ void wfq_help_peer(const gq_ring_view& R, const WfqCtx& x, u32 me, u64 pv) {
     u32 peer = (u32)(pv >> 32);
-    if (countdown > 1 && countdown <= x.help_delay) {
-        *priv = (pv & ~0xFFFFFFFFull) | (countdown - 1);
-        return;
-    }
     peer = (peer + 1) % x.k;
     if (peer == me) peer = (peer + 1) % x.k;
-    *priv = ((u64)peer << 32) | x.help_delay;
+    R.helpc[me] = ((u64)peer << 32) | x.help_delay;
     if (peer == me) return;
     u64* pr = rec_of(R, peer);
     const u64 pend = ld_acq(pr + kRPending);
@@ -421,6 +419,19 @@ static __device__ __noinline__ void wfq_maybe_help(const gq_ring_view& R, const 
     if (s1 != s2 || !(pend2 & 1)) return;
     if (x.stats) atomicAdd(x.stats + kStatHelps, 1ull);
     wfq_help_request(R, x, peer, s2, (pend2 & 2) != 0, init, (u32)idx, me);
+}
+
+// Help delay D (Section III-C): every D operations a thread inspects one peer
+// record.  The countdown is owner-only state in a compact per-thread array
+// (plain accesses; the 32 cursors of a warp share one 256-byte span).
+__device__ __forceinline__ void wfq_maybe_help(const gq_ring_view& R, const WfqCtx& x, u32 me) {
+    const u64 pv = R.helpc[me];
+    const u32 countdown = (u32)pv;
+    if (countdown > 1 && countdown <= x.help_delay) {
+        R.helpc[me] = pv - 1;
+        return;
+    }
+    wfq_help_peer(R, x, me, pv);
 }
 
 // Publishes a request in the caller's record, helps it to completion, and
@@ -465,7 +476,10 @@ __device__ int wfq_ring_enq(const gq_ring_view& R, const WfqCtx& x, u32 idx, u32
         if (wfq_try_enq<MATCH>(R, x, idx, &t) == kTryOk) return GQ_OK;
     if (patience == 0) t = (g_cnt(ld_rlx(R.tail)) - 1) & kCntMask;   // a ticket value r never held
     const u64 l = wfq_slow_request(R, x, me, true, t, idx);
-    if (!l) return GQ_ERR_TIMEOUT;
+    if (!l) {
+        latch_error(x.err, GQ_ERR_TIMEOUT);
+        return GQ_ERR_TIMEOUT;
+    }
     // make the entry visible to fast dequeuers if no dequeuer did it yet
     const u64 tf = l_cnt(l);
     u64* slot = R.slots + (tf & x.g.smask);
@@ -491,7 +505,10 @@ __device__ int wfq_ring_deq(const gq_ring_view& R, const WfqCtx& x, u32* idx, u3
     }
     if (patience == 0) h = (g_cnt(ld_rlx(R.head)) - 1) & kCntMask;
     const u64 l = wfq_slow_request(R, x, me, false, h, 0);
-    if (!l) return GQ_ERR_TIMEOUT;
+    if (!l) {
+        latch_error(x.err, GQ_ERR_TIMEOUT);
+        return GQ_ERR_TIMEOUT;
+    }
     // the outcome is at ticket hf: an item of its cycle there is ours to consume
     const u64 hf = l_cnt(l);
     u64* slot = R.slots + (hf & x.g.smask);

@@ -78,7 +78,7 @@ def test_workspace_grows_with_capacity_and_records():
     assert b - a == (2 * 2 * 8 + 8) * ((1 << 20) - (1 << 10))
     w1 = gq.gq_workspace_bytes(gq.GQ_WFQ, 1 << 10, 8, 1024)
     w2 = gq.gq_workspace_bytes(gq.GQ_WFQ, 1 << 10, 8, 2048)
-    assert w2 - w1 == 2 * 1024 * 128          # one 128-byte record per thread per ring
+    assert w2 - w1 == 2 * 1024 * (128 + 8)    # one 128-byte record and one help cursor per thread per ring
     y = gq.gq_workspace_bytes(gq.GQ_YMC, 1000, 8, 256)
     assert y >= 3 * 1001 * 8 + 256 * 128
     for v in (a, b, w1, w2, y):
