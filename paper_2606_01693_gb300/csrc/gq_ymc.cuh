@@ -98,10 +98,13 @@ __device__ __forceinline__ void ymc_advance(u64* C, u64 v) {
 
 enum { kYValue = 0, kYUnusable = 1, kYEmpty = 2 };
 
-// help_enq, unusual part: the cell is still empty after the spin or unusable.
-static __device__ __noinline__ int ymc_help_enq_slow(const YmcCtx& y, u32 me, u64 i, u64* v, u64 x) {
+// help_enq: settles cell i for the dequeuer `me` and returns kYValue with *v,
+// kYUnusable (try another cell), or kYEmpty (T <= i: no enqueue reached i).
+static __device__ __noinline__ int ymc_help_enq(const YmcCtx& y, u32 me, u64 i, u64* v) {
     u64* cv = y.val + i;
     u64* ce = y.enq + i;
+    u64 x = ld_acq(cv);
+    for (u32 s = 0; s < kYSpin && x == kVBot; ++s) x = ld_acq(cv);   // an enqueuer may be on its way
     if (x == kVBot) {
         if (!cas(cv, x, kVTop) && x != kVTop) { *v = x; return kYValue; }
         x = kVTop;
@@ -157,20 +160,6 @@ static __device__ __noinline__ int ymc_help_enq_slow(const YmcCtx& y, u32 me, u6
     if (x == kVTop) return kYUnusable;
     *v = x;
     return kYValue;
-}
-
-// help_enq: settles cell i for the dequeuer `me` and returns kYValue with *v,
-// kYUnusable (try another cell), or kYEmpty (T <= i: no enqueue reached i).
-// The common case (a value, possibly after a short spin) stays inline.
-__device__ __forceinline__ int ymc_help_enq(const YmcCtx& y, u32 me, u64 i, u64* v) {
-    u64* cv = y.val + i;
-    u64 x = ld_acq(cv);
-    for (u32 s = 0; s < kYSpin && x == kVBot; ++s) x = ld_acq(cv);   // an enqueuer may be on its way
-    if (x != kVBot && x != kVTop) {
-        *v = x;
-        return kYValue;
-    }
-    return ymc_help_enq_slow(y, me, i, v, x);
 }
 
 // Slow enqueue of v by thread me whose fast path last failed at cell id.
