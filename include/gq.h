@@ -183,6 +183,29 @@ int gq_get_stats(gq_handle h, gq_stats* out);
 /* Workspace size and whether the library owns it. */
 int gq_info(gq_handle h, uint64_t* workspace_bytes, int* library_owned);
 
+/* FIFO round trip that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory (for
+ * example code running while another framework owns the whole device
+ * allocator, or a service that must not allocate after start-up).
+ * It enqueues d_items[0..n) into a G-LFQ whose entire workspace lives in one
+ * file-scope static device array of the library (2.6 MB per device, held
+ * until the process exits), then attempts n dequeues; the dequeued values are
+ * written compacted to d_out[0..*d_num_out) in an unspecified order and
+ * *d_num_out is overwritten with their number (n when nothing fails).  Same
+ * result as gq_create + gq_enqueue_batch + gq_dequeue_batch on a G-LFQ of
+ * capacity >= n, without gq_create's allocation.
+ *   n <= 65536 (the array's capacity); larger n returns GQ_ERR_INVALID before
+ *   any work is launched.  d_items, d_out: n 8-byte elements; d_num_out: one
+ *   8-byte counter; all caller-owned device memory.
+ * Calls no cudaMalloc, cudaFree or allocating routine.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current and caches it; make that first call before any stream
+ * capture.  Every call shares the array and re-initialises it; calls that
+ * overlap on the GPU race and must be serialised by the caller.
+ * Errors: GQ_ERR_INVALID, GQ_ERR_CUDA. */
+int gq_fifo_static_roundtrip(const unsigned long long* d_items, uint64_t n, unsigned long long* d_out,
+                             unsigned long long* d_num_out, void* stream);
+
 /* Static description of a status code. */
 const char* gq_status_str(int status);
 

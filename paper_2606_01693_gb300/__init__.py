@@ -34,7 +34,7 @@ GQ_PEAK_SAME_ADDR_FAA, GQ_PEAK_COALESCED_CAS, GQ_PEAK_SCATTERED_CAS, GQ_PEAK_COA
 EXPORTS = [
     "gq_workspace_bytes", "gq_create", "gq_destroy", "gq_reset", "gq_enqueue_batch", "gq_dequeue_batch",
     "gq_sync_status", "gq_device_view", "gq_info", "gq_status_str", "gq_get_stats",
-    "gq_run", "gq_run_sequence", "gq_drain", "gq_atomic_peak",
+    "gq_run", "gq_run_sequence", "gq_drain", "gq_atomic_peak", "gq_fifo_static_roundtrip",
 ]
 
 
@@ -90,6 +90,7 @@ def load() -> ctypes.CDLL:
         "gq_run_sequence": [P, P, P, u64, P, P, P],
         "gq_drain": [P, P, u64, P, P],
         "gq_atomic_peak": [i32, u32, u32, u32, P, u64, P, P],
+        "gq_fifo_static_roundtrip": [P, u64, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -206,6 +207,13 @@ def gq_drain(h: int, out, count, max_items: int | None = None, stream=None) -> N
 def gq_atomic_peak(pattern: int, blocks: int, threads: int, iters: int, buf, sink, stream=None) -> None:
     _check(load().gq_atomic_peak(pattern, blocks, threads, iters, _ptr(buf), buf.numel(), _ptr(sink),
                                  _stream(stream)), "gq_atomic_peak")
+
+
+def gq_fifo_static_roundtrip(items, out, num_out, n: int | None = None, stream=None) -> None:
+    """FIFO round trip on the library's static device array (no allocation; n <= 65536)."""
+    n = items.numel() if n is None else n
+    _check(load().gq_fifo_static_roundtrip(_ptr(items), n, _ptr(out), _ptr(num_out), _stream(stream)),
+           "gq_fifo_static_roundtrip")
 
 
 # ---------------------------------------------------------------------------
