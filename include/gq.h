@@ -100,8 +100,12 @@ typedef struct {
     uint32_t max_threads;           /* number of per-thread records                */
     uint32_t patience_enq, patience_deq, help_delay;
     uint32_t batch_width;           /* WaveFAA group width                          */
-    uint32_t reserved0;
+    uint32_t ring_order;            /* log2(2n)                                    */
     uint64_t capacity;              /* ring: n; YMC: pool cells                    */
+    uint64_t slot_mask;             /* 2n - 1                                      */
+    uint64_t cycle_mask;            /* R - 1, R = 2^cycle_bits                     */
+    uint64_t cycle_half;            /* R / 2                                       */
+    int64_t thr_reset;              /* 3n - 1                                      */
     gq_ring_view aq, fq;            /* allocated-index ring, free-index ring       */
     void* data;                     /* payload array of n elements                 */
     unsigned int* err;              /* latched device error word                   */

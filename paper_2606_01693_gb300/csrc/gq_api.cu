@@ -152,7 +152,7 @@ __global__ void k_reset_slots(gq_dev q, u64 base_ticket) {
 // Batch kernels
 // ---------------------------------------------------------------------------
 template <class T, int KIND>
-__global__ void __launch_bounds__(256) k_enqueue_batch(gq_dev q, const T* __restrict__ items, u64 n,
+__global__ void __launch_bounds__(256) k_enqueue_batch(const __grid_constant__ gq_dev q, const T* __restrict__ items, u64 n,
                                                       int8_t* status, unsigned long long* num_ok) {
     const u64 stride = (u64)gridDim.x * blockDim.x;
     const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) k_enqueue_batch(gq_dev q, const T* __rest
 }
 
 template <class T, int KIND>
-__global__ void __launch_bounds__(256) k_dequeue_batch(gq_dev q, T* __restrict__ out, u64 n, int8_t* status,
+__global__ void __launch_bounds__(256) k_dequeue_batch(const __grid_constant__ gq_dev q, T* __restrict__ out, u64 n, int8_t* status,
                                                       unsigned long long* pos) {
     const u64 stride = (u64)gridDim.x * blockDim.x;
     const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -320,6 +320,13 @@ extern "C" int gq_create(int kind, uint64_t capacity, uint32_t elem_bytes, uint3
     d.help_delay = o.help_delay;
     d.batch_width = o.batch_width;
     d.capacity = capacity;
+    if (kind != GQ_YMC) {
+        d.ring_order = d.log2n + 1;
+        d.slot_mask = 2 * capacity - 1;
+        d.cycle_mask = (1ull << o.cycle_bits) - 1;
+        d.cycle_half = 1ull << (o.cycle_bits - 1);
+        d.thr_reset = (int64_t)(3 * capacity) - 1;
+    }
     void* b = h->ws;
     d.err = at<unsigned int>(b, h->lay.ctrl + kCtlErr * kLine);
     d.scratch = at<unsigned long long>(b, h->lay.ctrl + kCtlScratch * kLine);

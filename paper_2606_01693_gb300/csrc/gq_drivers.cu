@@ -32,9 +32,10 @@ __device__ __forceinline__ u32 mix32(u32 a, u32 b) {
 // 256 threads x 4 blocks per SM caps registers at 64: the rarely taken slow
 // paths of G-WFQ / G-WFQ-YMC may spill instead of halving occupancy.
 template <class T, int KIND>
-__global__ void __launch_bounds__(256, 4) k_run(gq_dev q, RunK a) {
+__global__ void __launch_bounds__(256, 4) k_run(const __grid_constant__ gq_dev q, const __grid_constant__ RunK a) {
     const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
-    u64 c_enq_ok = 0, c_full = 0, c_deq_ok = 0, c_empty = 0, s_enq = 0, s_deq = 0, c_err = 0;
+    u32 c_enq_ok = 0, c_full = 0, c_deq_ok = 0, c_empty = 0, c_err = 0;   // per-thread counts
+    u64 s_enq = 0, s_deq = 0;
     if (t < a.threads) {
         u32 nops = a.ops;
         bool producer = true;
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(256, 4) k_run(gq_dev q, RunK a) {
 }
 
 template <class T, int KIND>
-__global__ void k_sequence(gq_dev q, const uint8_t* kind, const u64* val, u64 n, int8_t* status, u64* out) {
+__global__ void k_sequence(const __grid_constant__ gq_dev q, const uint8_t* kind, const u64* val, u64 n, int8_t* status, u64* out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (u64 i = 0; i < n; ++i) {
         int s;
@@ -107,7 +108,7 @@ __global__ void k_sequence(gq_dev q, const uint8_t* kind, const u64* val, u64 n,
 }
 
 template <class T, int KIND>
-__global__ void k_drain(gq_dev q, u64* out, u64 max, unsigned long long* count) {
+__global__ void k_drain(const __grid_constant__ gq_dev q, u64* out, u64 max, unsigned long long* count) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     u64 k = 0;
     while (k < max) {

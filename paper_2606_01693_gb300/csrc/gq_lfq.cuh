@@ -38,30 +38,15 @@ constexpr u64 kSafe = 1ull << 32;
 constexpr u32 kBot = 0xFFFFFFFFu;
 constexpr u32 kBotC = 0xFFFFFFFEu;
 
-struct RingGeom {
-    u32 order;       // log2(2n)
-    u32 width;       // WaveFAA group width
-    u64 smask;       // 2n - 1
-    u64 cmask;       // R - 1
-    u64 half;        // R / 2
-    i64 thr_reset;   // 3n - 1
-};
-
-__device__ __forceinline__ RingGeom ring_geom(const gq_dev& q) {
-    RingGeom g;
-    g.order = q.log2n + 1;
-    g.width = q.batch_width;
-    g.smask = (2ull << q.log2n) - 1;
-    g.cmask = (1ull << q.cycle_bits) - 1;
-    g.half = 1ull << (q.cycle_bits - 1);
-    g.thr_reset = (i64)(3ull << q.log2n) - 1;
-    return g;
-}
+// Ring geometry is precomputed on the host into gq_dev (slot_mask = 2n - 1,
+// ring_order = log2(2n), cycle_mask = R - 1, cycle_half = R / 2, thr_reset =
+// 3n - 1) and read where it is used: a kernel parameter lives in the constant
+// bank, so the geometry costs no registers in the hot loops.
 
 // a is strictly older than b (modular, Lemma on cycle tags)
-__device__ __forceinline__ bool cyc_older(u64 a, u64 b, const RingGeom& g) {
-    const u64 d = (b - a) & g.cmask;
-    return d != 0 && d < g.half;
+__device__ __forceinline__ bool cyc_older(u64 a, u64 b, const gq_dev& q) {
+    const u64 d = (b - a) & q.cycle_mask;
+    return d != 0 && d < q.cycle_half;
 }
 
 __device__ __forceinline__ u64 lfq_cycle(u64 e) { return e >> 33; }
@@ -90,38 +75,38 @@ __device__ __forceinline__ void ring_catchup(const gq_ring_view& r, u64 tail, u6
 // Inner-ring enqueue of index `idx` (TryEnq of Algorithm 1, retried until it
 // succeeds).  Returns GQ_OK, or GQ_ERR_TIMEOUT if the retry bound expires.
 template <bool MATCH>
-__device__ int lfq_ring_enq(const gq_ring_view& r, const RingGeom& g, u32 idx, unsigned int* err) {
+__device__ int lfq_ring_enq(const gq_dev& q, const gq_ring_view& r, u32 idx) {
     for (u32 it = 0; it < kRetryLimit; ++it) {
-        const u64 t = warp_faa<MATCH>(r.tail, 1, g.width);
-        u64* slot = r.slots + (t & g.smask);
-        const u64 c = (t >> g.order) & g.cmask;
+        const u64 t = warp_faa<MATCH>(r.tail, 1, q.batch_width);
+        u64* slot = r.slots + (t & q.slot_mask);
+        const u64 c = (t >> q.ring_order) & q.cycle_mask;
         u64 e = ld_acq(slot);
         for (; it < kRetryLimit; ++it) {
-            if (!cyc_older(lfq_cycle(e), c, g) || lfq_index(e) < kBotC) break;
+            if (!cyc_older(lfq_cycle(e), c, q) || lfq_index(e) < kBotC) break;
             if (!(e & kSafe)) {
                 // an unsafe slot may be reused only if no dequeuer has passed t
                 if ((i64)(ld_rlx(r.head) - t) > 0) break;
             }
             if (cas(slot, e, lfq_entry(c, kSafe, idx))) {
-                if (ld_rlx(r.threshold) != g.thr_reset) thr_reset(r.threshold, g.thr_reset, err);
+                if (ld_rlx(r.threshold) != q.thr_reset) thr_reset(r.threshold, q.thr_reset, q.err);
                 return GQ_OK;
             }
             // CAS lost: e holds the current entry; re-evaluate the same ticket
         }
     }
-    latch_error(err, GQ_ERR_TIMEOUT);
+    latch_error(q.err, GQ_ERR_TIMEOUT);
     return GQ_ERR_TIMEOUT;
 }
 
 // Inner-ring dequeue (TryDeq of Algorithm 1, retried while it returns RETRY).
 // Returns GQ_OK with *idx, GQ_EMPTY, or GQ_ERR_TIMEOUT.
 template <bool MATCH>
-__device__ int lfq_ring_deq(const gq_ring_view& r, const RingGeom& g, u32* idx, unsigned int* err) {
+__device__ int lfq_ring_deq(const gq_dev& q, const gq_ring_view& r, u32* idx) {
     if (ld_rlx(r.threshold) < 0) return GQ_EMPTY;
     for (u32 it = 0; it < kRetryLimit; ++it) {
-        const u64 h = warp_faa<MATCH>(r.head, 1, g.width);
-        u64* slot = r.slots + (h & g.smask);
-        const u64 c = (h >> g.order) & g.cmask;
+        const u64 h = warp_faa<MATCH>(r.head, 1, q.batch_width);
+        u64* slot = r.slots + (h & q.slot_mask);
+        const u64 c = (h >> q.ring_order) & q.cycle_mask;
         u64 e = ld_acq(slot);
         for (; it < kRetryLimit; ++it) {
             const u64 ec = lfq_cycle(e);
@@ -134,7 +119,7 @@ __device__ int lfq_ring_deq(const gq_ring_view& r, const RingGeom& g, u32* idx, 
                 }
                 break;
             }
-            if (!cyc_older(ec, c, g)) break;         // slot already belongs to a later cycle
+            if (!cyc_older(ec, c, q)) break;         // slot already belongs to a later cycle
             // empty class: advance the slot to cycle c (still empty);
             // occupied by an older cycle: clear Safe so the enqueuer of t = h
             // does not reuse it once Head has passed h.
@@ -149,7 +134,7 @@ __device__ int lfq_ring_deq(const gq_ring_view& r, const RingGeom& g, u32* idx, 
         }
         if (thr_dec(r.threshold) <= 0) return GQ_EMPTY;
     }
-    latch_error(err, GQ_ERR_TIMEOUT);
+    latch_error(q.err, GQ_ERR_TIMEOUT);
     return GQ_ERR_TIMEOUT;
 }
 
@@ -167,9 +152,8 @@ __device__ __forceinline__ T data_load(const gq_dev& q, u32 i) {
 
 template <class T, bool MATCH>
 __device__ int lfq_enqueue(const gq_dev& q, T v) {
-    const RingGeom g = ring_geom(q);
     u32 i;
-    int s = lfq_ring_deq<MATCH>(q.fq, g, &i, q.err);
+    int s = lfq_ring_deq<MATCH>(q, q.fq, &i);
     if (s == GQ_EMPTY) return GQ_FULL;
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {                            // never expected: a corrupt ring entry
@@ -177,21 +161,20 @@ __device__ int lfq_enqueue(const gq_dev& q, T v) {
         return GQ_ERR_INVALID;
     }
     data_store<T>(q, i, v);                           // ordered before the release CAS in aq
-    return lfq_ring_enq<MATCH>(q.aq, g, i, q.err);
+    return lfq_ring_enq<MATCH>(q, q.aq, i);
 }
 
 template <class T, bool MATCH>
 __device__ int lfq_dequeue(const gq_dev& q, T* v) {
-    const RingGeom g = ring_geom(q);
     u32 i;
-    int s = lfq_ring_deq<MATCH>(q.aq, g, &i, q.err);
+    int s = lfq_ring_deq<MATCH>(q, q.aq, &i);
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {                            // never expected: a corrupt ring entry
         latch_error(q.err, GQ_ERR_INVALID);
         return GQ_ERR_INVALID;
     }
     *v = data_load<T>(q, i);                          // after the acquire on the aq slot
-    s = lfq_ring_enq<MATCH>(q.fq, g, i, q.err);       // release: the read precedes reuse
+    s = lfq_ring_enq<MATCH>(q, q.fq, i);              // release: the read precedes reuse
     return s == GQ_OK ? GQ_OK : s;
 }
 

@@ -73,13 +73,13 @@ __global__ void k_static_init(gq_dev q, unsigned long long* num_out) {
     }
 }
 
-__global__ void k_static_enq(gq_dev q, const unsigned long long* __restrict__ items, u64 n) {
+__global__ void k_static_enq(const __grid_constant__ gq_dev q, const unsigned long long* __restrict__ items, u64 n) {
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
         queue_enqueue<unsigned long long, GQ_LFQ>(q, items[k], 0);
 }
 
-__global__ void k_static_deq(gq_dev q, unsigned long long* __restrict__ out, u64 n, unsigned long long* num_out) {
+__global__ void k_static_deq(const __grid_constant__ gq_dev q, unsigned long long* __restrict__ out, u64 n, unsigned long long* num_out) {
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
         unsigned long long v;
@@ -112,6 +112,11 @@ extern "C" int gq_fifo_static_roundtrip(const unsigned long long* d_items, uint6
     q.max_threads = 1;
     q.batch_width = 32;
     q.capacity = cap;
+    q.ring_order = log2n + 1;
+    q.slot_mask = 2 * cap - 1;
+    q.cycle_mask = (1ull << 31) - 1;
+    q.cycle_half = 1ull << 30;
+    q.thr_reset = (int64_t)(3 * cap) - 1;
     q.err = reinterpret_cast<unsigned int*>(b);
     q.scratch = reinterpret_cast<unsigned long long*>(b + 128);
     q.aq.head = reinterpret_cast<unsigned long long*>(b + 2 * 128);

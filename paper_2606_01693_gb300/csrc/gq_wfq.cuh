@@ -106,24 +106,12 @@ constexpr u32 kSlowHard = 1u << 24;
 // Rare-path event counters kept in the queue's scratch line.
 enum { kStatSlowRequests = 1, kStatHelps = 2, kStatGlobalCasFail = 3 };
 
-struct WfqCtx {
-    RingGeom g;
-    u64 cmask, half;
-    u32 k;           // records
-    u32 help_delay;
-    u64 n;           // capacity (index bound)
-    unsigned int* err;
-    unsigned long long* stats;
-};
 
-__device__ __forceinline__ bool wc_older(u64 a, u64 b, const WfqCtx& x) {
-    const u64 d = (b - a) & x.cmask;
-    return d != 0 && d < x.half;
-}
+
 // newest of two notes (modular); used to keep Note within one cycle of the slot
-__device__ __forceinline__ u64 note_fresh(u64 note, u64 c, const WfqCtx& x) {
-    const u64 cm1 = (c - 1) & x.cmask;
-    return wc_older(note, cm1, x) ? cm1 : note;
+__device__ __forceinline__ u64 note_fresh(u64 note, u64 c, const gq_dev& q) {
+    const u64 cm1 = (c - 1) & q.cycle_mask;
+    return cyc_older(note, cm1, q) ? cm1 : note;
 }
 
 __device__ __forceinline__ u64* rec_of(const gq_ring_view& r, u32 id) { return r.rec + (u64)id * kRWords; }
@@ -154,7 +142,7 @@ __device__ __forceinline__ bool req_live(const gq_ring_view& R, u32 r, u64 seq) 
 // tried for r; on true it holds the new ticket.  Returns false when the request
 // is finished (FIN) or no longer live.
 static __device__ __noinline__ bool slow_faa(const gq_ring_view& R, int side, u32 r, u64 seq, u32 me, u64* v, i64* thld,
-                         const WfqCtx& x, u32* budget) {
+                         const gq_dev& q, u32* budget) {
     u64* G = side ? R.head : R.tail;
     u64* L = rec_of(R, r) + (side ? kRLocalHead : kRLocalTail);
     u64* P2 = rec_of(R, me) + (side ? kRP2Head : kRP2Tail);
@@ -203,9 +191,9 @@ static __device__ __noinline__ bool slow_faa(const gq_ring_view& R, int side, u3
             *v = c;
             return true;
         }
-        if (x.stats) atomicAdd(x.stats + kStatGlobalCasFail, 1ull);
+        if (q.scratch) atomicAdd(q.scratch + kStatGlobalCasFail, 1ull);
     }
-    latch_error(x.err, GQ_ERR_TIMEOUT);
+    latch_error(q.err, GQ_ERR_TIMEOUT);
     return false;
 }
 
@@ -220,14 +208,14 @@ __device__ __forceinline__ void wfq_catchup(const gq_ring_view& R, u64 head) {
 
 // Finishes the slow enqueue that installed entry e (Enq = 0) at ticket t:
 // FIN on its request at t (owner looked up by index), then Enq = 1.
-static __device__ __noinline__ void wfq_finalize(const gq_ring_view& R, u64* slot, u64 e, u64 t, const WfqCtx& x) {
+static __device__ __noinline__ void wfq_finalize(const gq_ring_view& R, u64* slot, u64 e, u64 t, const gq_dev& q) {
     const u32 i = w_idx(e);
-    if (i >= x.n) {
-        latch_error(x.err, GQ_ERR_INVALID);
+    if (i >= q.capacity) {
+        latch_error(q.err, GQ_ERR_INVALID);
         return;
     }
     const u64 o = ld_acq(R.owner + i);
-    if (o != 0 && o <= x.k) {
+    if (o != 0 && o <= q.max_threads) {
         u64 want = t << 2;
         cas(rec_of(R, (u32)o - 1) + kRLocalTail, want, want | kLFin);
     }
@@ -242,17 +230,17 @@ static __device__ __noinline__ void wfq_finalize(const gq_ring_view& R, u64* slo
 enum { kTryOk = 0, kTryEmpty = 2, kTryRetry = 3 };
 
 template <bool MATCH>
-__device__ int wfq_try_enq(const gq_ring_view& R, const WfqCtx& x, u32 idx, u64* t_out) {
-    const u64 t = warp_faa<MATCH>(R.tail, kGOne, x.g.width) >> kGThrBits & kCntMask;
+__device__ int wfq_try_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u64* t_out) {
+    const u64 t = warp_faa<MATCH>(R.tail, kGOne, q.batch_width) >> kGThrBits & kCntMask;
     *t_out = t;
-    u64* slot = R.slots + (t & x.g.smask);
-    const u64 c = (t >> x.g.order) & x.cmask;
+    u64* slot = R.slots + (t & q.slot_mask);
+    const u64 c = (t >> q.ring_order) & q.cycle_mask;
     u64 e = ld_acq(slot);
     for (u32 it = 0; it < kRetryLimit; ++it) {
-        if (!wc_older(w_cyc(e), c, x) || w_idx(e) < kWBotC) break;
+        if (!cyc_older(w_cyc(e), c, q) || w_idx(e) < kWBotC) break;
         if (!(e & kWSafe) && !cnt_le(g_cnt(ld_rlx(R.head)), t)) break;
-        if (cas(slot, e, wfq_entry(note_fresh(w_note(e), c, x), c, 1, 1, idx))) {
-            if (ld_rlx(R.threshold) != x.g.thr_reset) thr_reset(R.threshold, x.g.thr_reset, x.err);
+        if (cas(slot, e, wfq_entry(note_fresh(w_note(e), c, q), c, 1, 1, idx))) {
+            if (ld_rlx(R.threshold) != q.thr_reset) thr_reset(R.threshold, q.thr_reset, q.err);
             return kTryOk;
         }
     }
@@ -260,34 +248,34 @@ __device__ int wfq_try_enq(const gq_ring_view& R, const WfqCtx& x, u32 idx, u64*
 }
 
 // Consumes the item of ticket h in `slot` (its cycle already checked).
-__device__ __forceinline__ u32 wfq_consume(const gq_ring_view& R, u64* slot, u64 e, u64 h, const WfqCtx& x) {
-    if (!(e & kWEnq)) wfq_finalize(R, slot, e, h, x);
+__device__ __forceinline__ u32 wfq_consume(const gq_ring_view& R, u64* slot, u64 e, u64 h, const gq_dev& q) {
+    if (!(e & kWEnq)) wfq_finalize(R, slot, e, h, q);
     return w_idx(aref<u64>(*slot).fetch_or(kWBotC, kRlx));   // e was read with acquire
 }
 
 template <bool MATCH>
-__device__ int wfq_try_deq(const gq_ring_view& R, const WfqCtx& x, u32* idx, u64* h_out) {
-    const u64 h = warp_faa<MATCH>(R.head, kGOne, x.g.width) >> kGThrBits & kCntMask;
+__device__ int wfq_try_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u64* h_out) {
+    const u64 h = warp_faa<MATCH>(R.head, kGOne, q.batch_width) >> kGThrBits & kCntMask;
     *h_out = h;
-    u64* slot = R.slots + (h & x.g.smask);
-    const u64 c = (h >> x.g.order) & x.cmask;
+    u64* slot = R.slots + (h & q.slot_mask);
+    const u64 c = (h >> q.ring_order) & q.cycle_mask;
     u64 e = ld_acq(slot);
     for (u32 it = 0; it < kRetryLimit; ++it) {
         const u64 ec = w_cyc(e);
         if (ec == c) {
             if (w_idx(e) < kWBotC) {
-                *idx = wfq_consume(R, slot, e, h, x);
+                *idx = wfq_consume(R, slot, e, h, q);
                 return kTryOk;
             }
             break;
         }
-        if (!wc_older(ec, c, x)) break;
+        if (!cyc_older(ec, c, q)) break;
         const u64 ne = (w_idx(e) >= kWBotC)
-                           ? wfq_entry(note_fresh(w_note(e), c, x), c, e & kWSafe, 1, kWBot)
+                           ? wfq_entry(note_fresh(w_note(e), c, q), c, e & kWSafe, 1, kWBot)
                            : (e & ~kWSafe);
         if (cas(slot, e, ne)) break;
         if (it + 1 == kRetryLimit) {
-            latch_error(x.err, GQ_ERR_TIMEOUT);
+            latch_error(q.err, GQ_ERR_TIMEOUT);
             return kTryRetry;
         }
     }
@@ -305,9 +293,9 @@ __device__ int wfq_try_deq(const gq_ring_view& R, const WfqCtx& x, u32* idx, u64
 enum { kSlowDone = 0, kSlowNext = 1 };
 
 // TryEnqSlow: install idx at ticket t (Enq = 0), or rule the slot out (Note).
-static __device__ __noinline__ int wfq_try_enq_slow(const gq_ring_view& R, const WfqCtx& x, u32 r, u64 t, u32 idx) {
-    u64* slot = R.slots + (t & x.g.smask);
-    const u64 c = (t >> x.g.order) & x.cmask;
+static __device__ __noinline__ int wfq_try_enq_slow(const gq_ring_view& R, const gq_dev& q, u32 r, u64 t, u32 idx) {
+    u64* slot = R.slots + (t & q.slot_mask);
+    const u64 c = (t >> q.ring_order) & q.cycle_mask;
     u64 e = ld_acq(slot);
     for (u32 it = 0; it < kRetryLimit; ++it) {
         const u64 ec = w_cyc(e);
@@ -320,11 +308,11 @@ static __device__ __noinline__ int wfq_try_enq_slow(const gq_ring_view& R, const
             }
             return kSlowNext;
         }
-        if (!wc_older(ec, c, x) || !wc_older(w_note(e), c, x)) return kSlowNext;
+        if (!cyc_older(ec, c, q) || !cyc_older(w_note(e), c, q)) return kSlowNext;
         const bool usable = (w_idx(e) >= kWBotC) && ((e & kWSafe) || cnt_le(g_cnt(ld_rlx(R.head)), t));
         if (usable) {
-            if (cas(slot, e, wfq_entry(note_fresh(w_note(e), c, x), c, 1, 0, idx))) {
-                if (ld_rlx(R.threshold) != x.g.thr_reset) thr_reset(R.threshold, x.g.thr_reset, x.err);
+            if (cas(slot, e, wfq_entry(note_fresh(w_note(e), c, q), c, 1, 0, idx))) {
+                if (ld_rlx(R.threshold) != q.thr_reset) thr_reset(R.threshold, q.thr_reset, q.err);
                 u64 want = t << 2;
                 cas(rec_of(R, r) + kRLocalTail, want, want | kLFin);
                 return kSlowDone;
@@ -337,10 +325,10 @@ static __device__ __noinline__ int wfq_try_enq_slow(const gq_ring_view& R, const
 }
 
 // TryDeqSlow: find the outcome of head ticket h for request r; FIN marks it.
-static __device__ __noinline__ int wfq_try_deq_slow(const gq_ring_view& R, const WfqCtx& x, u32 r, u64 h) {
-    u64* slot = R.slots + (h & x.g.smask);
+static __device__ __noinline__ int wfq_try_deq_slow(const gq_ring_view& R, const gq_dev& q, u32 r, u64 h) {
+    u64* slot = R.slots + (h & q.slot_mask);
     u64* L = rec_of(R, r) + kRLocalHead;
-    const u64 c = (h >> x.g.order) & x.cmask;
+    const u64 c = (h >> q.ring_order) & q.cycle_mask;
     u64 e = ld_acq(slot);
     for (u32 it = 0; it < kRetryLimit; ++it) {
         const u64 ec = w_cyc(e);
@@ -352,17 +340,17 @@ static __device__ __noinline__ int wfq_try_deq_slow(const gq_ring_view& R, const
             }
             break;                               // ruled out at cycle c already
         }
-        if (!wc_older(ec, c, x)) break;
+        if (!cyc_older(ec, c, q)) break;
         u64 ne;
         if (w_idx(e) >= kWBotC) {
-            ne = wfq_entry(note_fresh(w_note(e), c, x), c, e & kWSafe, 1, kWBot);
+            ne = wfq_entry(note_fresh(w_note(e), c, q), c, e & kWSafe, 1, kWBot);
         } else {
             ne = e & ~kWSafe;
-            if (wc_older(w_note(e), c, x)) ne = w_set_note(ne, c);
+            if (cyc_older(w_note(e), c, q)) ne = w_set_note(ne, c);
         }
         if (cas(slot, e, ne)) break;
         if (it + 1 == kRetryLimit) {
-            latch_error(x.err, GQ_ERR_TIMEOUT);
+            latch_error(q.err, GQ_ERR_TIMEOUT);
             return kSlowNext;
         }
     }
@@ -386,27 +374,27 @@ static __device__ __noinline__ int wfq_try_deq_slow(const gq_ring_view& R, const
 // if another helper moved the request on first (for a dequeue, an EMPTY
 // observation at one moment and a "not empty" one at another are both valid),
 // so the loop always returns to SlowFAA, which stops only once FIN is set.
-static __device__ __noinline__ void wfq_help_request(const gq_ring_view& R, const WfqCtx& x, u32 r, u64 seq, bool enq,
+static __device__ __noinline__ void wfq_help_request(const gq_ring_view& R, const gq_dev& q, u32 r, u64 seq, bool enq,
                                                      u64 init, u32 idx, u32 me) {
     u64 v = init;
     const int side = enq ? 0 : 1;
     i64* thld = enq ? nullptr : R.threshold;
     u32 budget = kSlowHard;
     while (budget) {
-        if (!slow_faa(R, side, r, seq, me, &v, thld, x, &budget)) return;
-        if (enq) wfq_try_enq_slow(R, x, r, v, idx);
-        else wfq_try_deq_slow(R, x, r, v);
+        if (!slow_faa(R, side, r, seq, me, &v, thld, q, &budget)) return;
+        if (enq) wfq_try_enq_slow(R, q, r, v, idx);
+        else wfq_try_deq_slow(R, q, r, v);
     }
-    latch_error(x.err, GQ_ERR_TIMEOUT);
+    latch_error(q.err, GQ_ERR_TIMEOUT);
 }
 
 // Inspects the next peer record (round robin) and helps it if a request is
 // pending with matching sequence fields.
-static __device__ __noinline__ void wfq_help_peer(const gq_ring_view& R, const WfqCtx& x, u32 me, u64 pv) {
+static __device__ __noinline__ void wfq_help_peer(const gq_ring_view& R, const gq_dev& q, u32 me, u64 pv) {
     u32 peer = (u32)(pv >> 32);
-    peer = (peer + 1) % x.k;
-    if (peer == me) peer = (peer + 1) % x.k;
-    R.helpc[me] = ((u64)peer << 32) | x.help_delay;
+    peer = (peer + 1) % q.max_threads;
+    if (peer == me) peer = (peer + 1) % q.max_threads;
+    R.helpc[me] = ((u64)peer << 32) | q.help_delay;
     if (peer == me) return;
     u64* pr = rec_of(R, peer);
     const u64 pend = ld_acq(pr + kRPending);
@@ -417,26 +405,26 @@ static __device__ __noinline__ void wfq_help_peer(const gq_ring_view& R, const W
     const u64 pend2 = ld_acq(pr + kRPending);
     const u64 s1 = ld_acq(pr + kRSeq1);
     if (s1 != s2 || !(pend2 & 1)) return;
-    if (x.stats) atomicAdd(x.stats + kStatHelps, 1ull);
-    wfq_help_request(R, x, peer, s2, (pend2 & 2) != 0, init, (u32)idx, me);
+    if (q.scratch) atomicAdd(q.scratch + kStatHelps, 1ull);
+    wfq_help_request(R, q, peer, s2, (pend2 & 2) != 0, init, (u32)idx, me);
 }
 
 // Help delay D (Section III-C): every D operations a thread inspects one peer
 // record.  The countdown is owner-only state in a compact per-thread array
 // (plain accesses; the 32 cursors of a warp share one 256-byte span).
-__device__ __forceinline__ void wfq_maybe_help(const gq_ring_view& R, const WfqCtx& x, u32 me) {
+__device__ __forceinline__ void wfq_maybe_help(const gq_ring_view& R, const gq_dev& q, u32 me) {
     const u64 pv = R.helpc[me];
     const u32 countdown = (u32)pv;
-    if (countdown > 1 && countdown <= x.help_delay) {
+    if (countdown > 1 && countdown <= q.help_delay) {
         R.helpc[me] = pv - 1;
         return;
     }
-    wfq_help_peer(R, x, me, pv);
+    wfq_help_peer(R, q, me, pv);
 }
 
 // Publishes a request in the caller's record, helps it to completion, and
 // retires it.  Returns the final local word (FIN set) or 0 on timeout.
-static __device__ __noinline__ u64 wfq_slow_request(const gq_ring_view& R, const WfqCtx& x, u32 me, bool enq, u64 init, u32 idx) {
+static __device__ __noinline__ u64 wfq_slow_request(const gq_ring_view& R, const gq_dev& q, u32 me, bool enq, u64 init, u32 idx) {
     u64* rec = rec_of(R, me);
     const u64 seq = ld_rlx(rec + kRSeq1);
     u64* L = rec + (enq ? kRLocalTail : kRLocalHead);
@@ -446,44 +434,32 @@ static __device__ __noinline__ u64 wfq_slow_request(const gq_ring_view& R, const
     st_rel(L, init << 2);
     st_rel(rec + kRSeq2, seq);
     st_rel(rec + kRPending, 1ull | (enq ? 2ull : 0ull));
-    if (x.stats) atomicAdd(x.stats + kStatSlowRequests, 1ull);
-    wfq_help_request(R, x, me, seq, enq, init, idx, me);
+    if (q.scratch) atomicAdd(q.scratch + kStatSlowRequests, 1ull);
+    wfq_help_request(R, q, me, seq, enq, init, idx, me);
     const u64 l = ld_acq(L);
     st_rel(rec + kRPending, 0);
     st_rel(rec + kRSeq1, seq + 1);
     return (l & kLFin) ? l : 0;
 }
 
-__device__ __forceinline__ WfqCtx wfq_ctx(const gq_dev& q) {
-    WfqCtx x;
-    x.g = ring_geom(q);
-    x.cmask = (1ull << q.cycle_bits) - 1;
-    x.half = 1ull << (q.cycle_bits - 1);
-    x.k = q.max_threads;
-    x.n = q.capacity;
-    x.help_delay = q.help_delay;
-    x.err = q.err;
-    x.stats = q.scratch;
-    return x;
-}
 
 // Inner-ring enqueue of index idx by thread `me`.
 template <bool MATCH>
-__device__ int wfq_ring_enq(const gq_ring_view& R, const WfqCtx& x, u32 idx, u32 me, u32 patience) {
-    wfq_maybe_help(R, x, me);
+__device__ int wfq_ring_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u32 me, u32 patience) {
+    wfq_maybe_help(R, q, me);
     u64 t = 0;
     for (u32 p = 0; p < patience; ++p)
-        if (wfq_try_enq<MATCH>(R, x, idx, &t) == kTryOk) return GQ_OK;
+        if (wfq_try_enq<MATCH>(R, q, idx, &t) == kTryOk) return GQ_OK;
     if (patience == 0) t = (g_cnt(ld_rlx(R.tail)) - 1) & kCntMask;   // a ticket value r never held
-    const u64 l = wfq_slow_request(R, x, me, true, t, idx);
+    const u64 l = wfq_slow_request(R, q, me, true, t, idx);
     if (!l) {
-        latch_error(x.err, GQ_ERR_TIMEOUT);
+        latch_error(q.err, GQ_ERR_TIMEOUT);
         return GQ_ERR_TIMEOUT;
     }
     // make the entry visible to fast dequeuers if no dequeuer did it yet
     const u64 tf = l_cnt(l);
-    u64* slot = R.slots + (tf & x.g.smask);
-    const u64 c = (tf >> x.g.order) & x.cmask;
+    u64* slot = R.slots + (tf & q.slot_mask);
+    const u64 c = (tf >> q.ring_order) & q.cycle_mask;
     u64 e = ld_acq(slot);
     for (u32 it = 0; it < kRetryLimit; ++it) {
         if (w_cyc(e) != c || w_idx(e) != idx || (e & kWEnq)) break;
@@ -494,28 +470,28 @@ __device__ int wfq_ring_enq(const gq_ring_view& R, const WfqCtx& x, u32 idx, u32
 
 // Inner-ring dequeue by thread `me`: GQ_OK with *idx, or GQ_EMPTY.
 template <bool MATCH>
-__device__ int wfq_ring_deq(const gq_ring_view& R, const WfqCtx& x, u32* idx, u32 me, u32 patience) {
+__device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u32 me, u32 patience) {
     if (ld_rlx(R.threshold) < 0) return GQ_EMPTY;
-    wfq_maybe_help(R, x, me);
+    wfq_maybe_help(R, q, me);
     u64 h = 0;
     for (u32 p = 0; p < patience; ++p) {
-        const int s = wfq_try_deq<MATCH>(R, x, idx, &h);
+        const int s = wfq_try_deq<MATCH>(R, q, idx, &h);
         if (s == kTryOk) return GQ_OK;
         if (s == kTryEmpty) return GQ_EMPTY;
     }
     if (patience == 0) h = (g_cnt(ld_rlx(R.head)) - 1) & kCntMask;
-    const u64 l = wfq_slow_request(R, x, me, false, h, 0);
+    const u64 l = wfq_slow_request(R, q, me, false, h, 0);
     if (!l) {
-        latch_error(x.err, GQ_ERR_TIMEOUT);
+        latch_error(q.err, GQ_ERR_TIMEOUT);
         return GQ_ERR_TIMEOUT;
     }
     // the outcome is at ticket hf: an item of its cycle there is ours to consume
     const u64 hf = l_cnt(l);
-    u64* slot = R.slots + (hf & x.g.smask);
-    const u64 c = (hf >> x.g.order) & x.cmask;
+    u64* slot = R.slots + (hf & q.slot_mask);
+    const u64 c = (hf >> q.ring_order) & q.cycle_mask;
     const u64 e = ld_acq(slot);
     if (w_cyc(e) == c && w_idx(e) < kWBotC) {
-        *idx = wfq_consume(R, slot, e, hf, x);
+        *idx = wfq_consume(R, slot, e, hf, q);
         return GQ_OK;
     }
     return GQ_EMPTY;
@@ -527,9 +503,8 @@ __device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
     }
-    const WfqCtx x = wfq_ctx(q);
     u32 i;
-    int s = wfq_ring_deq<MATCH>(q.fq, x, &i, tid, q.patience_deq);
+    int s = wfq_ring_deq<MATCH>(q.fq, q, &i, tid, q.patience_deq);
     if (s == GQ_EMPTY) return GQ_FULL;
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {
@@ -537,7 +512,7 @@ __device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid) {
         return GQ_ERR_INVALID;
     }
     data_store<T>(q, i, v);
-    return wfq_ring_enq<MATCH>(q.aq, x, i, tid, q.patience_enq);
+    return wfq_ring_enq<MATCH>(q.aq, q, i, tid, q.patience_enq);
 }
 
 template <class T, bool MATCH>
@@ -546,16 +521,15 @@ __device__ int wfq_dequeue(const gq_dev& q, T* v, u32 tid) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
     }
-    const WfqCtx x = wfq_ctx(q);
     u32 i;
-    int s = wfq_ring_deq<MATCH>(q.aq, x, &i, tid, q.patience_deq);
+    int s = wfq_ring_deq<MATCH>(q.aq, q, &i, tid, q.patience_deq);
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {
         latch_error(q.err, GQ_ERR_INVALID);
         return GQ_ERR_INVALID;
     }
     *v = data_load<T>(q, i);
-    s = wfq_ring_enq<MATCH>(q.fq, x, i, tid, q.patience_enq);
+    s = wfq_ring_enq<MATCH>(q.fq, q, i, tid, q.patience_enq);
     return s == GQ_OK ? GQ_OK : s;
 }
 

@@ -63,28 +63,17 @@ enum : int {
     kYWords = 16
 };
 
-struct YmcCtx {
-    u64* T;
-    u64* H;
-    u64* val;
-    u64* enq;
-    u64* deq;
-    u64* rec;
-    u64 cells;     // last valid cell index
-    u32 k;
-    u32 width;
-    unsigned int* err;
-};
 
-__device__ __forceinline__ u64* yrec(const YmcCtx& y, u32 r) { return y.rec + (u64)r * kYWords; }
+
+__device__ __forceinline__ u64* yrec(const gq_dev& q, u32 r) { return q.ymc_rec + (u64)r * kYWords; }
 __device__ __forceinline__ u64 ytag(u64 id, u32 r) { return (id << 24) | (u64)(r + 1); }
 __device__ __forceinline__ u32 ytag_thread(u64 e) { return (u32)(e & ((1u << 24) - 1)) - 1; }
 __device__ __forceinline__ i64 ytag_id(u64 e) { return (i64)(e >> 24); }
 __device__ __forceinline__ i64 ld_i(u64* p) { return (i64)ld_acq(p); }
 
-__device__ __forceinline__ bool ycell_ok(const YmcCtx& y, u64 i) {
-    if (i >= 1 && i <= y.cells) return true;
-    latch_error(y.err, GQ_ERR_POOL_EXHAUSTED);
+__device__ __forceinline__ bool ycell_ok(const gq_dev& q, u64 i) {
+    if (i >= 1 && i <= q.capacity) return true;
+    latch_error(q.err, GQ_ERR_POOL_EXHAUSTED);
     return false;
 }
 
@@ -100,9 +89,9 @@ enum { kYValue = 0, kYUnusable = 1, kYEmpty = 2 };
 
 // help_enq: settles cell i for the dequeuer `me` and returns kYValue with *v,
 // kYUnusable (try another cell), or kYEmpty (T <= i: no enqueue reached i).
-static __device__ __noinline__ int ymc_help_enq(const YmcCtx& y, u32 me, u64 i, u64* v) {
-    u64* cv = y.val + i;
-    u64* ce = y.enq + i;
+static __device__ __noinline__ int ymc_help_enq(const gq_dev& q, u32 me, u64 i, u64* v) {
+    u64* cv = q.cell_val + i;
+    u64* ce = q.cell_enq + i;
     u64 x = ld_acq(cv);
     for (u32 s = 0; s < kYSpin && x == kVBot; ++s) x = ld_acq(cv);   // an enqueuer may be on its way
     if (x == kVBot) {
@@ -115,21 +104,21 @@ static __device__ __noinline__ int ymc_help_enq(const YmcCtx& y, u32 me, u64 i, 
     // the cell is unusable for fast enqueues: offer it to a pending slow enqueue
     u64 e = ld_acq(ce);
     if (e == kRefBot) {
-        u64* mine = yrec(y, me);
+        u64* mine = yrec(q, me);
         u32 p = (u32)mine[kYEh];                   // private cursors: plain access
-        i64 s = ld_i(yrec(y, p) + kYErId);
+        i64 s = ld_i(yrec(q, p) + kYErId);
         if (mine[kYEi] != 0 && (i64)mine[kYEi] != s) {
             mine[kYEi] = 0;
-            p = (p + 1) % y.k;
+            p = (p + 1) % q.max_threads;
             mine[kYEh] = p;
-            s = ld_i(yrec(y, p) + kYErId);
+            s = ld_i(yrec(q, p) + kYErId);
         }
         u64 want = kRefBot;
         if (s > 0 && (u64)s <= i && !cas(ce, want, ytag((u64)s, p)) && want != ytag((u64)s, p)) {
             mine[kYEi] = (u64)s;                   // keep helping this request
         } else {
             mine[kYEi] = 0;
-            mine[kYEh] = (p + 1) % y.k;
+            mine[kYEh] = (p + 1) % q.max_threads;
         }
         e = ld_acq(ce);
         if (e == kRefBot) {
@@ -137,9 +126,9 @@ static __device__ __noinline__ int ymc_help_enq(const YmcCtx& y, u32 me, u64 i, 
             if (cas(ce, b, kRefTop)) e = kRefTop; else e = b;
         }
     }
-    if (e == kRefTop) return (ld_acq(y.T) <= i) ? kYEmpty : kYUnusable;
+    if (e == kRefTop) return (ld_acq(q.ymc_tail) <= i) ? kYEmpty : kYUnusable;
     // the cell names request instance (id_e of thread r)
-    u64* er = yrec(y, ytag_thread(e));
+    u64* er = yrec(q, ytag_thread(e));
     const i64 id_e = ytag_id(e);
     i64 ei = ld_i(er + kYErId);
     const u64 ev = ld_acq(er + kYErVal);
@@ -150,11 +139,11 @@ static __device__ __noinline__ int ymc_help_enq(const YmcCtx& y, u32 me, u64 i, 
         else ei = (i64)cur;
     }
     if (claimed || (ei == -(i64)i && ld_acq(cv) == kVTop)) {
-        ymc_advance(y.T, i);
+        ymc_advance(q.ymc_tail, i);
         st_rel(cv, ev);                            // commit the request's value in cell i
     } else if (ei != -(i64)i) {
         // the instance was satisfied elsewhere: this cell stays unusable for good
-        if (ld_acq(cv) == kVTop && ld_acq(y.T) <= i) return kYEmpty;
+        if (ld_acq(cv) == kVTop && ld_acq(q.ymc_tail) <= i) return kYEmpty;
     }
     x = ld_acq(cv);
     if (x == kVTop) return kYUnusable;
@@ -163,23 +152,23 @@ static __device__ __noinline__ int ymc_help_enq(const YmcCtx& y, u32 me, u64 i, 
 }
 
 // Slow enqueue of v by thread me whose fast path last failed at cell id.
-static __device__ __noinline__ int ymc_enq_slow(const YmcCtx& y, u32 me, u64 v, u64 id) {
-    u64* er = yrec(y, me);
+static __device__ __noinline__ int ymc_enq_slow(const gq_dev& q, u32 me, u64 v, u64 id) {
+    u64* er = yrec(q, me);
     // release: a helper that reads this value must also see the commit of this
     // thread's previous request (its cell value), see ymc_help_enq
     st_rel(er + kYErVal, v);
     st_rel(er + kYErId, id);
     u64 i = id;
     for (u32 it = 0; it < kRetryLimit && ld_i(er + kYErId) > 0; ++it) {
-        i = faa_rlx(y.T, 1);
-        if (!ycell_ok(y, i)) {
+        i = faa_rlx(q.ymc_tail, 1);
+        if (!ycell_ok(q, i)) {
             // withdraw the request unless a helper has already claimed a cell
             u64 cur = id;
             if (cas(er + kYErId, cur, 0)) return GQ_ERR_POOL_EXHAUSTED;
             break;
         }
         u64 b = kRefBot;
-        if (cas(y.enq + i, b, ytag(id, me)) && ld_acq(y.val + i) != kVTop) {
+        if (cas(q.cell_enq + i, b, ytag(id, me)) && ld_acq(q.cell_val + i) != kVTop) {
             u64 cur = id;
             cas(er + kYErId, cur, (u64)(-(i64)i));   // claim cell i (a helper may have claimed another)
             break;
@@ -187,18 +176,18 @@ static __device__ __noinline__ int ymc_enq_slow(const YmcCtx& y, u32 me, u64 v, 
     }
     const i64 done = ld_i(er + kYErId);
     if (done >= 0) {
-        latch_error(y.err, GQ_ERR_TIMEOUT);
+        latch_error(q.err, GQ_ERR_TIMEOUT);
         return GQ_ERR_TIMEOUT;
     }
     const u64 c = (u64)(-done);
-    ymc_advance(y.T, c);
-    st_rel(y.val + c, v);
+    ymc_advance(q.ymc_tail, c);
+    st_rel(q.cell_val + c, v);
     return GQ_OK;
 }
 
 // Helps the dequeue request of thread p (called by me).
-static __device__ __noinline__ void ymc_help_deq(const YmcCtx& y, u32 me, u32 p) {
-    u64* dr = yrec(y, p);
+static __device__ __noinline__ void ymc_help_deq(const gq_dev& q, u32 me, u32 p) {
+    u64* dr = yrec(q, p);
     i64 idx = ld_i(dr + kYDrIdx);
     const i64 id = ld_i(dr + kYDrId);
     if (id <= 0 || idx < id) return;
@@ -208,10 +197,10 @@ static __device__ __noinline__ void ymc_help_deq(const YmcCtx& y, u32 me, u32 p)
         u32 jt = 0;
         for (; jt < kRetryLimit && idx == old && cand == 0; ++jt) {
             ++i;
-            if (!ycell_ok(y, (u64)i)) return;
+            if (!ycell_ok(q, (u64)i)) return;
             u64 v;
-            const int s = ymc_help_enq(y, me, (u64)i, &v);
-            if (s == kYEmpty || (s == kYValue && ld_acq(y.deq + i) == kRefBot)) cand = i;
+            const int s = ymc_help_enq(q, me, (u64)i, &v);
+            if (s == kYEmpty || (s == kYValue && ld_acq(q.cell_deq + i) == kRefBot)) cand = i;
             else idx = ld_i(dr + kYDrIdx);
         }
         if (jt == kRetryLimit) break;   // never claim the request's own first cell unannounced
@@ -223,7 +212,7 @@ static __device__ __noinline__ void ymc_help_deq(const YmcCtx& y, u32 me, u32 p)
         }
         if (idx < 0 || ld_i(dr + kYDrId) != id) return;    // completed
         u64 b = kRefBot;
-        if (ld_acq(y.val + idx) == kVTop || cas(y.deq + idx, b, (u64)p + 2) || b == (u64)p + 2) {
+        if (ld_acq(q.cell_val + idx) == kVTop || cas(q.cell_deq + idx, b, (u64)p + 2) || b == (u64)p + 2) {
             u64 cur = (u64)idx;
             cas(dr + kYDrIdx, cur, (u64)(-idx));
             return;
@@ -231,23 +220,9 @@ static __device__ __noinline__ void ymc_help_deq(const YmcCtx& y, u32 me, u32 p)
         old = idx;
         if (idx >= i) i = idx;
     }
-    latch_error(y.err, GQ_ERR_TIMEOUT);
+    latch_error(q.err, GQ_ERR_TIMEOUT);
 }
 
-__device__ __forceinline__ YmcCtx ymc_ctx(const gq_dev& q) {
-    YmcCtx y;
-    y.T = q.ymc_tail;
-    y.H = q.ymc_head;
-    y.val = q.cell_val;
-    y.enq = q.cell_enq;
-    y.deq = q.cell_deq;
-    y.rec = q.ymc_rec;
-    y.cells = q.capacity;
-    y.k = q.max_threads;
-    y.width = q.batch_width;
-    y.err = q.err;
-    return y;
-}
 
 template <class T, bool MATCH>
 __device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid) {
@@ -257,16 +232,15 @@ __device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid) {
     }
     const u64 x = (u64)v;
     if (x >= kVTop) return GQ_ERR_RESERVED_VALUE;
-    const YmcCtx y = ymc_ctx(q);
     u64 id = 0;
     for (u32 p = 0; p <= q.patience_enq; ++p) {
-        const u64 i = warp_faa<MATCH>(y.T, 1, y.width);
-        if (!ycell_ok(y, i)) return GQ_ERR_POOL_EXHAUSTED;
+        const u64 i = warp_faa<MATCH>(q.ymc_tail, 1, q.batch_width);
+        if (!ycell_ok(q, i)) return GQ_ERR_POOL_EXHAUSTED;
         u64 b = kVBot;
-        if (aref<u64>(y.val[i]).compare_exchange_strong(b, x, kRel, kRlx)) return GQ_OK;
+        if (aref<u64>(q.cell_val[i]).compare_exchange_strong(b, x, kRel, kRlx)) return GQ_OK;
         id = i;
     }
-    return ymc_enq_slow(y, tid, x, id);
+    return ymc_enq_slow(q, tid, x, id);
 }
 
 template <class T, bool MATCH>
@@ -275,41 +249,40 @@ __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
     }
-    const YmcCtx y = ymc_ctx(q);
     u64 id = 0, v = 0;
     int res = kYUnusable;
     for (u32 p = 0; p <= q.patience_deq && res == kYUnusable; ++p) {
-        const u64 i = warp_faa<MATCH>(y.H, 1, y.width);
-        if (!ycell_ok(y, i)) return GQ_ERR_POOL_EXHAUSTED;
-        res = ymc_help_enq(y, tid, i, &v);
+        const u64 i = warp_faa<MATCH>(q.ymc_head, 1, q.batch_width);
+        if (!ycell_ok(q, i)) return GQ_ERR_POOL_EXHAUSTED;
+        res = ymc_help_enq(q, tid, i, &v);
         if (res == kYValue) {
             u64 b = kRefBot;
-            if (!cas(y.deq + i, b, kRefTop)) res = kYUnusable;   // a slow dequeue took it
+            if (!cas(q.cell_deq + i, b, kRefTop)) res = kYUnusable;   // a slow dequeue took it
         }
         id = i;
     }
     if (res == kYUnusable) {
         // slow path: publish <id, idx = id> and help it to completion
-        u64* dr = yrec(y, tid);
+        u64* dr = yrec(q, tid);
         st_rel(dr + kYDrId, id);
         st_rel(dr + kYDrIdx, id);
-        ymc_help_deq(y, tid, tid);
+        ymc_help_deq(q, tid, tid);
         const i64 idx = ld_i(dr + kYDrIdx);
         if (idx >= 0) {
-            latch_error(y.err, GQ_ERR_TIMEOUT);
+            latch_error(q.err, GQ_ERR_TIMEOUT);
             return GQ_ERR_TIMEOUT;
         }
         const u64 c = (u64)(-idx);
-        ymc_advance(y.H, c);
-        v = ld_acq(y.val + c);
+        ymc_advance(q.ymc_head, c);
+        v = ld_acq(q.cell_val + c);
         res = (v == kVTop) ? kYEmpty : kYValue;
     }
     if (res == kYEmpty) return GQ_EMPTY;
     // after a successful dequeue, help one peer's dequeue request
-    u64* mine = yrec(y, tid);
+    u64* mine = yrec(q, tid);
     const u32 peer = (u32)mine[kYDh];
-    mine[kYDh] = (peer + 1) % y.k;
-    if (peer != tid) ymc_help_deq(y, tid, peer);
+    mine[kYDh] = (peer + 1) % q.max_threads;
+    if (peer != tid) ymc_help_deq(q, tid, peer);
     *out = (T)v;
     return GQ_OK;
 }
