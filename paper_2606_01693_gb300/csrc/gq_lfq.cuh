@@ -9,8 +9,11 @@
 //     bit  32      Safe
 //     bits 31..0   Index:  a value < 2^32 - 2,  BOT = 2^32 - 1 (empty),
 //                          BOTC = 2^32 - 2 (consumed)
-// Consume is an atomic OR of BOTC into the index bits: any index becomes BOTC
-// or BOT, both of the "empty class", and the Cycle and Safe bits are kept.
+// Consume marks the index field BOTC and keeps the Cycle and Safe bits: a CAS
+// from the entry the dequeuer read to the same entry with index BOTC, falling
+// back to an atomic OR of BOTC into the index bits (any index then becomes
+// BOTC or BOT, both of the "empty class") if a concurrent Safe change made the
+// CAS fail.  Writing exactly BOTC keeps a consumed slot's value predictable.
 // Cycles are compared modulo R (a is older than b iff 0 < (b - a) mod R < R/2),
 // sound while the live skew on a slot stays below R/2 (Lemma "Reduced-width
 // cycle tags").
@@ -27,7 +30,11 @@
 //     adjacent 128-byte lines and coalesce into few L2 atomic requests; sCQ's
 //     cache-line remapping of consecutive tickets is deliberately not used;
 //   * a CAS that fails on a slot re-evaluates the same ticket with the value it
-//     returned (no ticket is burned for a lost race on a still-usable slot).
+//     returned (no ticket is burned for a lost race on a still-usable slot);
+//   * an enqueue first CASes against the slot's most likely value, "consumed in
+//     the previous cycle" <c-1, Safe, BOTC>, instead of loading it: a right
+//     guess saves one L2 round trip, a wrong one returns the current value,
+//     which the protocol then evaluates exactly as a load's result.
 #pragma once
 
 #include "gq_atomics.cuh"
@@ -80,18 +87,21 @@ __device__ int lfq_ring_enq(const gq_dev& q, const gq_ring_view& r, u32 idx) {
         const u64 t = warp_faa<MATCH>(r.tail, 1, q.batch_width);
         u64* slot = r.slots + (t & q.slot_mask);
         const u64 c = (t >> q.ring_order) & q.cycle_mask;
-        u64 e = ld_acq(slot);
-        for (; it < kRetryLimit; ++it) {
+        const u64 ne = lfq_entry(c, kSafe, idx);
+        u64 e = lfq_entry((c - 1) & q.cycle_mask, kSafe, kBotC);   // predicted current value
+        bool done = cas(slot, e, ne);
+        for (; !done && it < kRetryLimit; ++it) {
             if (!cyc_older(lfq_cycle(e), c, q) || lfq_index(e) < kBotC) break;
             if (!(e & kSafe)) {
                 // an unsafe slot may be reused only if no dequeuer has passed t
                 if ((i64)(ld_rlx(r.head) - t) > 0) break;
             }
-            if (cas(slot, e, lfq_entry(c, kSafe, idx))) {
-                if (ld_rlx(r.threshold) != q.thr_reset) thr_reset(r.threshold, q.thr_reset, q.err);
-                return GQ_OK;
-            }
+            done = cas(slot, e, ne);
             // CAS lost: e holds the current entry; re-evaluate the same ticket
+        }
+        if (done) {
+            if (ld_rlx(r.threshold) != q.thr_reset) thr_reset(r.threshold, q.thr_reset, q.err);
+            return GQ_OK;
         }
     }
     latch_error(q.err, GQ_ERR_TIMEOUT);
@@ -112,9 +122,10 @@ __device__ int lfq_ring_deq(const gq_dev& q, const gq_ring_view& r, u32* idx) {
             const u64 ec = lfq_cycle(e);
             if (ec == c) {
                 if (lfq_index(e) < kBotC) {          // Consume and return the index
+                    *idx = lfq_index(e);
                     // relaxed: the acquire load of e already ordered the payload read
-                    const u64 before = aref<u64>(*slot).fetch_or(kBotC, kRlx);
-                    *idx = lfq_index(before);
+                    if (!aref<u64>(*slot).compare_exchange_strong(e, (e & ~0xFFFFFFFFull) | kBotC, kRlx, kRlx))
+                        aref<u64>(*slot).fetch_or(kBotC, kRlx);
                     return GQ_OK;
                 }
                 break;

@@ -235,22 +235,32 @@ __device__ int wfq_try_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u64*
     *t_out = t;
     u64* slot = R.slots + (t & q.slot_mask);
     const u64 c = (t >> q.ring_order) & q.cycle_mask;
-    u64 e = ld_acq(slot);
-    for (u32 it = 0; it < kRetryLimit; ++it) {
+    // predicted current value: consumed in the previous cycle, Note one older
+    const u64 cm1 = (c - 1) & q.cycle_mask;
+    u64 e = wfq_entry((c - 2) & q.cycle_mask, cm1, 1, 1, kWBotC);
+    bool done = cas(slot, e, wfq_entry(cm1, c, 1, 1, idx));
+    for (u32 it = 0; !done && it < kRetryLimit; ++it) {
         if (!cyc_older(w_cyc(e), c, q) || w_idx(e) < kWBotC) break;
         if (!(e & kWSafe) && !cnt_le(g_cnt(ld_rlx(R.head)), t)) break;
-        if (cas(slot, e, wfq_entry(note_fresh(w_note(e), c, q), c, 1, 1, idx))) {
-            if (ld_rlx(R.threshold) != q.thr_reset) thr_reset(R.threshold, q.thr_reset, q.err);
-            return kTryOk;
-        }
+        done = cas(slot, e, wfq_entry(note_fresh(w_note(e), c, q), c, 1, 1, idx));
     }
-    return kTryRetry;
+    if (!done) return kTryRetry;
+    if (ld_rlx(R.threshold) != q.thr_reset) thr_reset(R.threshold, q.thr_reset, q.err);
+    return kTryOk;
 }
 
 // Consumes the item of ticket h in `slot` (its cycle already checked).
+// Consume: index field to BOTC, other fields kept (CAS from the entry read,
+// OR as the fallback); e was read with acquire, so the consume can be relaxed.
 __device__ __forceinline__ u32 wfq_consume(const gq_ring_view& R, u64* slot, u64 e, u64 h, const gq_dev& q) {
-    if (!(e & kWEnq)) wfq_finalize(R, slot, e, h, q);
-    return w_idx(aref<u64>(*slot).fetch_or(kWBotC, kRlx));   // e was read with acquire
+    if (!(e & kWEnq)) {
+        wfq_finalize(R, slot, e, h, q);
+        e |= kWEnq;
+    }
+    const u32 i = w_idx(e);
+    if (!aref<u64>(*slot).compare_exchange_strong(e, (e & ~(u64)kWIdxMask) | kWBotC, kRlx, kRlx))
+        aref<u64>(*slot).fetch_or(kWBotC, kRlx);
+    return i;
 }
 
 template <bool MATCH>
