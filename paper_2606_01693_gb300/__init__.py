@@ -35,6 +35,7 @@ EXPORTS = [
     "gq_workspace_bytes", "gq_create", "gq_destroy", "gq_reset", "gq_enqueue_batch", "gq_dequeue_batch",
     "gq_sync_status", "gq_device_view", "gq_info", "gq_status_str", "gq_get_stats",
     "gq_run", "gq_run_sequence", "gq_drain", "gq_atomic_peak", "gq_fifo_static_roundtrip",
+    "gq_bfs",
 ]
 
 
@@ -91,6 +92,7 @@ def load() -> ctypes.CDLL:
         "gq_drain": [P, P, u64, P, P],
         "gq_atomic_peak": [i32, u32, u32, u32, P, u64, P, P],
         "gq_fifo_static_roundtrip": [P, u64, P, P, P],
+        "gq_bfs": [P, P, u64, P, P, u32, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -214,6 +216,15 @@ def gq_fifo_static_roundtrip(items, out, num_out, n: int | None = None, stream=N
     n = items.numel() if n is None else n
     _check(load().gq_fifo_static_roundtrip(_ptr(items), n, _ptr(out), _ptr(num_out), _stream(stream)),
            "gq_fifo_static_roundtrip")
+
+
+GQ_BFS_UNREACHED = 0xFFFFFFFF
+
+
+def gq_bfs(q_a: int, q_b: int, offsets, adj, src: int, dist, stats=None, stream=None) -> None:
+    """Level-synchronous BFS with two alternating frontier queues (4-byte queues of one kind)."""
+    _check(load().gq_bfs(q_a, q_b, offsets.numel() - 1, _ptr(offsets), _ptr(adj), src, _ptr(dist), _ptr(stats),
+                         _stream(stream)), "gq_bfs")
 
 
 # ---------------------------------------------------------------------------

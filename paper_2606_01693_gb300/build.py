@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgq.so")
-SOURCES = ["gq_api.cu", "gq_drivers.cu", "gq_peaks.cu", "gq_static.cu"]
+SOURCES = ["gq_api.cu", "gq_drivers.cu", "gq_peaks.cu", "gq_static.cu", "gq_apps.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

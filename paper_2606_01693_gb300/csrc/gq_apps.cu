@@ -1,0 +1,174 @@
+// Applications on the queues (include/gq_apps.h): level-synchronous BFS with
+// two alternating frontier queues (Section V-B).
+//
+// GPU-first structure: one cooperative persistent kernel runs every level; a
+// device-wide barrier (bounded wait) separates levels, so no host round trip
+// happens per level.  Per level only as many warps dequeue as the frontier
+// needs (ceil(F / 32)), which keeps the end-of-level EMPTY dequeues few (a
+// G-WFQ-YMC EMPTY dequeue costs a pool cell).  A lane that dequeued a vertex of
+// degree < 32 scans it alone; vertices of degree >= 32 are scanned by the whole
+// warp with coalesced adjacency loads.  A neighbour is claimed with a CAS on
+// its distance word (UNREACHED -> level + 1); distances are unique, so any
+// claim order yields the same distances.
+#include <cuda_runtime.h>
+
+#include "../../include/gq_apps.h"
+#include "gq_host.h"
+#include "gq_ops.cuh"
+
+using namespace gqd;
+
+namespace {
+
+constexpr u32 kUnreached = 0xFFFFFFFFu;
+constexpr u32 kBarrierSpinLimit = 1u << 26;   // x ~100 ns sleeps: a few seconds
+
+// Control words in the first queue's scratch line (words 8..15).
+enum { kCtlBarCount = 0, kCtlBarGen = 1, kCtlFront0 = 2, kCtlFront1 = 3, kCtlFront2 = 4, kCtlErr = 5 };
+
+// Device-wide barrier for a cooperative launch: the last block to arrive
+// resets the count and bumps the generation; the others wait for it, at most
+// kBarrierSpinLimit sleeps, after which they latch an error and go on.
+__device__ __forceinline__ bool grid_barrier(u64* ctl, u32 nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const u64 gen = ld_acq(ctl + kCtlBarGen);
+        __threadfence();
+        if (atomicAdd(reinterpret_cast<unsigned long long*>(ctl + kCtlBarCount), 1ull) + 1 == nblocks) {
+            st_rlx(ctl + kCtlBarCount, 0);
+            st_rel(ctl + kCtlBarGen, gen + 1);
+        } else {
+            u32 it = 0;
+            while (ld_acq(ctl + kCtlBarGen) == gen) {
+                if (++it > kBarrierSpinLimit) {
+                    atomicCAS(reinterpret_cast<unsigned long long*>(ctl + kCtlErr), 0ull, 1ull);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = ok && ld_acq(ctl + kCtlErr) == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int KIND>
+__device__ __forceinline__ void bfs_visit(const gq_dev& nxt, u32* dist, u32 w, u32 next_level, u32 tid, u32* cnt) {
+    if (aref<u32>(dist[w]).load(kRlx) != kUnreached) return;
+    if (atomicCAS(dist + w, kUnreached, next_level) != kUnreached) return;
+    if (queue_enqueue<unsigned int, KIND>(nxt, w, tid) == GQ_OK) ++*cnt;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, const __grid_constant__ gq_dev qb, u64 n,
+                                             const u64* __restrict__ off, const u32* __restrict__ adj, u32 src,
+                                             u32* dist, unsigned long long* stats) {
+    u64* ctl = reinterpret_cast<u64*>(qa.scratch) + 8;
+    const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 nthreads = gridDim.x * blockDim.x;
+    const u32 lane = threadIdx.x & 31;
+    const u32 warp = tid >> 5;
+    const u32 nwarps = nthreads >> 5;
+    for (u64 v = tid; v < n; v += nthreads) dist[v] = kUnreached;
+    if (!grid_barrier(ctl, gridDim.x)) return;
+    if (tid == 0) {
+        dist[src] = 0;
+        if (queue_enqueue<unsigned int, KIND>(qa, src, 0) == GQ_OK) st_rlx(ctl + kCtlFront0, 1);
+    }
+    if (!grid_barrier(ctl, gridDim.x)) return;
+    u64 edges = 0, reached = 0;
+    u32 level = 0;
+    for (;; ++level) {
+        const u64 frontier = ld_acq(ctl + kCtlFront0 + level % 3);
+        if (frontier == 0) break;
+        reached += (tid == 0) ? frontier : 0;
+        if (tid == 0) st_rlx(ctl + kCtlFront0 + (level + 2) % 3, 0);   // read by all during level - 1
+        const gq_dev& cur = (level & 1) ? qb : qa;
+        const gq_dev& nxt = (level & 1) ? qa : qb;
+        u32 cnt = 0;
+        const u64 want = (frontier + 31) / 32;
+        if (warp < want || warp < 1) {
+            bool active = true;
+            for (u32 round = 0; round < kRetryLimit; ++round) {
+                unsigned int v = 0;
+                int s = GQ_EMPTY;
+                if (active) s = queue_dequeue<unsigned int, KIND>(cur, &v, tid);
+                active = active && (s == GQ_OK);   // an EMPTY is final within a level
+                const u32 got = __ballot_sync(0xffffffffu, active);
+                if (!got) break;
+                u64 b = 0, e = 0;
+                if (active) {
+                    b = off[v];
+                    e = off[v + 1];
+                    if (e - b < 32) {                 // low degree: this lane alone
+                        edges += e - b;
+                        for (u64 k = b; k < e; ++k) bfs_visit<KIND>(nxt, dist, adj[k], level + 1, tid, &cnt);
+                    }
+                }
+                u32 big = __ballot_sync(0xffffffffu, active && (e - b >= 32));
+                while (big) {                         // high degree: the whole warp, coalesced
+                    const u32 owner = __ffs(big) - 1;
+                    big &= big - 1;
+                    const u64 bb = __shfl_sync(0xffffffffu, b, owner);
+                    const u64 ee = __shfl_sync(0xffffffffu, e, owner);
+                    if (lane == 0) edges += ee - bb;
+                    for (u64 k = bb + lane; k < ee; k += 32) bfs_visit<KIND>(nxt, dist, adj[k], level + 1, tid, &cnt);
+                    __syncwarp();
+                }
+            }
+        }
+        warp_add_full(reinterpret_cast<unsigned long long*>(ctl + kCtlFront0 + (level + 1) % 3), cnt);
+        if (!grid_barrier(ctl, gridDim.x)) return;
+    }
+    if (stats) warp_add_full(stats + 2, edges);
+    if (tid == 0 && stats) {
+        stats[0] = level;
+        stats[1] = reached;
+        stats[3] = ld_acq(ctl + kCtlErr);
+    }
+}
+
+template <int KIND>
+int launch_bfs(gq_handle ha, gq_handle hb, uint64_t n, const uint64_t* off, const uint32_t* adj, uint32_t src,
+               uint32_t* dist, unsigned long long* stats, cudaStream_t st) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs<KIND>, 256, 0) != cudaSuccess || occ < 1)
+        return GQ_ERR_CUDA;
+    uint64_t grid = (uint64_t)occ * (uint64_t)ha->sm_count;
+    if (KIND != GQ_LFQ) {
+        const uint64_t rec = ha->dev.max_threads < hb->dev.max_threads ? ha->dev.max_threads : hb->dev.max_threads;
+        if (grid > rec / 256) grid = rec / 256;
+    }
+    if (grid < 1) return GQ_ERR_TOO_MANY_THREADS;
+    gq_dev qa = ha->dev, qb = hb->dev;
+    const u64* o = reinterpret_cast<const u64*>(off);
+    const u32* a = reinterpret_cast<const u32*>(adj);
+    void* args[] = {&qa, &qb, &n, (void*)&o, (void*)&a, &src, &dist, &stats};
+    if (cudaLaunchCooperativeKernel((const void*)k_bfs<KIND>, dim3((unsigned)grid), dim3(256), args, 0, st) != cudaSuccess)
+        return GQ_ERR_CUDA;
+    return gq_check_launch();
+}
+
+}  // namespace
+
+extern "C" int gq_bfs(gq_handle q_a, gq_handle q_b, uint64_t n, const uint64_t* d_offsets, const uint32_t* d_adj,
+                      uint32_t src, uint32_t* d_dist, unsigned long long* d_stats, void* stream) {
+    if (!q_a || !q_b || q_a == q_b || !d_offsets || !d_dist || n == 0 || n >= 0xFFFFFFFFull || src >= n)
+        return GQ_ERR_INVALID;
+    if (q_a->dev.kind != q_b->dev.kind || q_a->dev.elem_bytes != 4 || q_b->dev.elem_bytes != 4 ||
+        q_a->device != q_b->device)
+        return GQ_ERR_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(q_a->dev.scratch + 8, 0, 8 * sizeof(unsigned long long), st) != cudaSuccess) return GQ_ERR_CUDA;
+    if (d_stats && cudaMemsetAsync(d_stats, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess) return GQ_ERR_CUDA;
+    switch (q_a->dev.kind) {
+        case GQ_LFQ: return launch_bfs<GQ_LFQ>(q_a, q_b, n, d_offsets, d_adj, src, d_dist, d_stats, st);
+        case GQ_WFQ: return launch_bfs<GQ_WFQ>(q_a, q_b, n, d_offsets, d_adj, src, d_dist, d_stats, st);
+        default: return launch_bfs<GQ_YMC>(q_a, q_b, n, d_offsets, d_adj, src, d_dist, d_stats, st);
+    }
+}

@@ -103,16 +103,65 @@ def _csr_from_pairs(n: int, src: np.ndarray, dst: np.ndarray) -> tuple[np.ndarra
 
 
 def grid_csr(width: int, height: int) -> tuple[np.ndarray, np.ndarray]:
-    """4-neighbour 2-D grid; vertex id = row * width + col."""
-    v = np.arange(width * height, dtype=np.int64)
+    """4-neighbour 2-D grid; vertex id = row * width + col; neighbour lists in
+    increasing id order (up, left, right, down)."""
+    n = width * height
+    v = np.arange(n, dtype=np.int64)
     r, c = v // width, v % width
-    srcs, dsts = [], []
-    for dr, dc in ((0, 1), (0, -1), (1, 0), (-1, 0)):
-        rr, cc = r + dr, c + dc
-        ok = (rr >= 0) & (rr < height) & (cc >= 0) & (cc < width)
-        srcs.append(v[ok])
-        dsts.append(rr[ok] * width + cc[ok])
-    return _csr_from_pairs(width * height, np.concatenate(srcs), np.concatenate(dsts))
+    has = [r > 0, c > 0, c < width - 1, r < height - 1]
+    nb = [v - width, v - 1, v + 1, v + width]
+    deg = sum(h.astype(np.int64) for h in has)
+    offsets = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(deg, out=offsets[1:])
+    adj = np.empty(int(offsets[-1]), dtype=np.uint32)
+    pos = offsets[:-1].astype(np.int64).copy()
+    for h, w in zip(has, nb):
+        adj[pos[h]] = w[h]
+        pos[h] += 1
+    return offsets, adj
+
+
+_clib = None
+
+
+def _lib():
+    """Loads (building if needed) the C++ generator helpers in gen.cpp."""
+    global _clib
+    if _clib is None:
+        import ctypes
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        so = os.path.join(here, "libsynth.so")
+        srcf = os.path.join(here, "gen.cpp")
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(srcf):
+            tmp = so + ".tmp%d" % os.getpid()
+            subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-o", tmp, srcf])
+            os.replace(tmp, so)
+        L = ctypes.CDLL(so)
+        P, i64, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64
+        L.synth_rmat_pairs.argtypes = [ctypes.c_int, i64, u64, u64, u64, u64, P, P]
+        L.synth_rmat_pairs.restype = i64
+        L.synth_csr.argtypes = [i64, i64, P, P, P, P]
+        L.synth_csr.restype = i64
+        _clib = L
+    return _clib
+
+
+def rmat_csr_fast(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+                  seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Same graph as rmat_csr, generated by the C++ helper (multi-threaded)."""
+    L = _lib()
+    n = 1 << scale
+    m = edge_factor * n
+    src = np.empty(2 * m, dtype=np.uint32)
+    dst = np.empty(2 * m, dtype=np.uint32)
+    k = L.synth_rmat_pairs(scale, m, seed & 0xFFFFFFFFFFFFFFFF, int(a * 2**32), int((a + b) * 2**32),
+                           int((a + b + c) * 2**32), src.ctypes.data, dst.ctypes.data)
+    offsets = np.empty(n + 1, dtype=np.uint64)
+    adj = np.empty(k, dtype=np.uint32)
+    e = L.synth_csr(n, k, src.ctypes.data, dst.ctypes.data, offsets.ctypes.data, adj.ctypes.data)
+    return offsets, adj[:e].copy()
 
 
 def rmat_csr(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared_symbols():
     names = set()
-    for h in ("gq.h", "gq_drivers.h"):
+    for h in ("gq.h", "gq_drivers.h", "gq_apps.h"):
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         for m in re.finditer(r"^\s*(?:int|const char\*|void)\s+(gq_\w+)\s*\(", src, flags=re.M):

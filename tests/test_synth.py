@@ -49,3 +49,20 @@ def test_rmat_symmetric_simple():
     for v in range(n):                              # sorted neighbour lists
         nb = adj[off[v]:off[v + 1]]
         assert (np.diff(nb.astype(np.int64)) > 0).all()
+
+
+def test_rmat_fast_generator_matches_reference_definition():
+    for scale, seed in ((8, 1), (11, 7)):
+        o1, a1 = synth.rmat_csr(scale, seed=seed)
+        o2, a2 = synth.rmat_csr_fast(scale, seed=seed)
+        assert (o1 == o2).all() and (a1 == a2).all()
+
+
+def test_grid_neighbours_sorted_and_symmetric():
+    off, adj = synth.grid_csr(7, 5)
+    n = len(off) - 1
+    src = np.repeat(np.arange(n), np.diff(off.astype(np.int64)))
+    for v in range(n):
+        nb = adj[off[v]:off[v + 1]]
+        assert (np.diff(nb.astype(np.int64)) > 0).all()
+    assert set(zip(src.tolist(), adj.tolist())) == set(zip(adj.tolist(), src.tolist()))
