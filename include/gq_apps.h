@@ -27,8 +27,9 @@ extern "C" {
 
 /* Breadth-first search from `src`.
  *   q_a, q_b: two empty queues of the same kind with 4-byte elements, each of
- *     capacity >= the largest frontier (|V| always suffices; G-WFQ-YMC: pool
- *     cells >= 2 |V| + 64 * (number of levels + 1) * threads / 32), and
+ *     capacity >= the largest frontier (|V| always suffices); G-WFQ-YMC, whose
+ *     cells are never reused, needs a pool of about 3 |V| + 64 (levels + 1)
+ *     cells (each level's dequeuers end with one EMPTY ticket per lane), and
  *     max_threads >= the launch's threads (gq_bfs uses at most
  *     min(max_threads, resident threads) threads).  They are left empty.
  *   n: vertices (< 2^32 - 1); d_offsets[n + 1] (uint64), d_adj[d_offsets[n]]

@@ -16,7 +16,7 @@ KINDS = list(gq.READY_KINDS)
 
 def _queues(kind, n, max_threads=1 << 20, levels_hint=64):
     if kind == "ymc":
-        cap = 2 * n + 64 * (levels_hint + 1) * (max_threads // 32) // 8 + (1 << 16)
+        cap = 3 * n + 64 * (levels_hint + 1) + (1 << 16)
     else:
         cap = 1 << max(1, (n - 1).bit_length())
         if kind == "wfq":
