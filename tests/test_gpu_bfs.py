@@ -14,13 +14,15 @@ DEV = "cuda"
 KINDS = list(gq.READY_KINDS)
 
 
-def _queues(kind, n, max_threads=1 << 20, levels_hint=64):
+def _queues(kind, n, max_threads=1 << 19, levels_hint=64):
+    # records for every resident thread (152 SMs x 2048 < 2^19)
     if kind == "ymc":
         cap = 3 * n + 64 * (levels_hint + 1) + (1 << 16)
     else:
         cap = 1 << max(1, (n - 1).bit_length())
         if kind == "wfq":
-            cap = min(cap, 1 << 23)
+            # G-WFQ's cycle soundness R > D k / n + 6 needs n > 64 k / 2^19
+            cap = min(max(cap, 1 << 12), 1 << 23)
     return gq.Queue(kind, cap, 4, max_threads), gq.Queue(kind, cap, 4, max_threads)
 
 
