@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-threads", type=int, default=1 << 17, help="logical threads in the CPU sample")
+    p.add_argument("--no-apps", action="store_true", help="skip the application measurements (BFS)")
     return p.parse_args()
 
 
@@ -118,6 +119,49 @@ def cpu_baseline(T, K, seed, cpu_threads):
     return {"value": succ / secs / 1e6, "unit": "Mops/s", "cores": nt, "kind": "oracle",
             "sample": "mutex-guarded std::deque, same 50/50 schedule, first %d of %d threads x %d ops "
                       "(%d ops, %.2f s)" % (Ts, T, K, Ts * K, secs)}
+
+
+def bench_apps(gq, synth, kinds, dev, reps=3):
+    """Level-synchronous BFS over two frontier queues of each kind (untimed for
+    the headline): R-MAT scale 22 (edge factor 16) from vertex 0 and the
+    4096 x 4096 grid from its corner; ms per search and scanned edges per second."""
+    import torch
+    out = {}
+    graphs = {"rmat22": synth.rmat_csr_fast(22, seed=0), "grid4096": synth.grid_csr(4096, 4096)}
+    for gname, (off, adj) in graphs.items():
+        n = len(off) - 1
+        d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+        d_adj = torch.from_numpy(adj.view(np.int32)).to(dev)
+        dist = torch.empty(n, dtype=torch.int32, device=dev)
+        stats = torch.zeros(4, dtype=torch.int64, device=dev)
+        levels_hint = 8192 if gname.startswith("grid") else 64
+        for k in kinds:
+            if k == "ymc":
+                cap = 3 * n + 64 * (levels_hint + 1) + (1 << 16)
+            else:
+                cap = min(1 << max(12, (n - 1).bit_length()), 1 << 23)
+            qa, qb = gq.Queue(k, cap, 4, 1 << 19), gq.Queue(k, cap, 4, 1 << 19)
+            gq.gq_bfs(qa.handle, qb.handle, d_off, d_adj, 0, dist, stats)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(reps):
+                qa.reset()
+                qb.reset()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                gq.gq_bfs(qa.handle, qb.handle, d_off, d_adj, 0, dist, stats)
+                e1.record()
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            st = stats.cpu().numpy()
+            assert qa.sync_status() == 0 and qb.sync_status() == 0 and st[3] == 0
+            t = float(np.median(ms))
+            out["bfs_%s_%s" % (gname, k)] = {"ms": round(t, 3), "levels": int(st[0]), "reached": int(st[1]),
+                                              "edges_scanned": int(st[2]),
+                                              "gteps": round(float(st[2]) / (t * 1e-3) / 1e9, 3)}
+            qa.close()
+            qb.close()
+    return out
 
 
 def run_reference(args):
@@ -359,6 +403,10 @@ def main():
                "how": "per queue: reset, pinned H2D of 2^20 items, gq_enqueue_batch, gq_dequeue_batch, "
                       "D2H of values and counts; wall clock over %d steps" % args.steps}
 
+    apps = None
+    if not args.no_apps:
+        apps = bench_apps(gq, synth, kinds, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(T, K, args.seed, args.cpu_threads)
@@ -375,7 +423,7 @@ def main():
                            "l2": "flushed between timed steps (256 MiB write); queue state re-initialised inside "
                                  "each step"},
                 "roofline": roofline, "peaks": peaks, "per_queue": per_queue, "sweep": sweep,
-                "cpu_baseline": cpu, "e2e": e2e,
+                "cpu_baseline": cpu, "e2e": e2e, "apps": apps,
                 "gpu_launches": args.steps * sum(launches_per_step[k] for k in kinds),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
