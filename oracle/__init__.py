@@ -10,7 +10,7 @@ What it computes (see ``oracle.h`` for the C entry points):
   * ``check_log``      exactly-once / per-producer-order / no-overtaking checks
   * ``mutex_run``      mutex-guarded std::deque on N host threads (timed baseline)
   * ``bfs``            textbook sequential BFS
-  * ``render``         sequential CPU ray tracer (when built)
+  * ``render_pixels``  sequential CPU ray tracer (per-pixel radiance)
 """
 from __future__ import annotations
 
@@ -35,6 +35,14 @@ class Report(ctypes.Structure):
                 ("first_index", ctypes.c_int64)]
 
 
+class RtScene(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("max_bounces", ctypes.c_int32),
+                ("nspheres", ctypes.c_int32), ("cam_x", ctypes.c_float), ("cam_y", ctypes.c_float),
+                ("cam_z", ctypes.c_float), ("scale_x", ctypes.c_float), ("scale_y", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("centre", ctypes.c_void_p), ("radius", ctypes.c_void_p),
+                ("albedo", ctypes.c_void_p)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -52,9 +60,8 @@ def lib():
         L.orc_mutex_run.restype = ctypes.c_double
         L.orc_bfs.argtypes = [i64, P, P, u32, P]
         L.orc_bfs.restype = i64
-        if hasattr(L, "orc_render"):
-            L.orc_render.argtypes = [i32, i32, i32, P, P, P, i32, u64, P]
-            L.orc_render.restype = i64
+        L.orc_render_pixels.argtypes = [ctypes.POINTER(RtScene), P, i64, P, P, i32]
+        L.orc_render_pixels.restype = None
         _lib = L
     return _lib
 
@@ -108,6 +115,24 @@ def mutex_run(mode, T, K, sched=None, producers=0, ops_of=None, cap=0, nthreads=
     ops_of = None if ops_of is None else np.ascontiguousarray(ops_of, dtype=np.int64)
     secs = lib().orc_mutex_run(mode, T, K, _p(sched), producers, _p(ops_of), cap, nthreads, _p(counts))
     return secs, counts, nthreads
+
+
+def render_pixels(scene: dict, width, height, pixels, max_bounces=8, seed=0, threads=None):
+    """Radiance (m, 3) float32 and segment counts of the listed pixel indices."""
+    if threads is None:
+        threads = os.cpu_count() or 1
+    centre = np.ascontiguousarray(scene["centre"], dtype=np.float32)
+    radius = np.ascontiguousarray(scene["radius"], dtype=np.float32)
+    albedo = np.ascontiguousarray(scene["albedo"], dtype=np.float32)
+    cam = scene.get("camera", (0.5, 0.5, -1.5))
+    sx, sy = scene["scale"]
+    S = RtScene(width, height, max_bounces, len(radius), cam[0], cam[1], cam[2], sx, sy, seed,
+                _p(centre), _p(radius), _p(albedo))
+    pixels = np.ascontiguousarray(pixels, dtype=np.int64)
+    rgb = np.zeros((len(pixels), 3), dtype=np.float32)
+    segs = np.zeros(len(pixels), dtype=np.int32)
+    lib().orc_render_pixels(ctypes.byref(S), _p(pixels), len(pixels), _p(rgb), _p(segs), threads)
+    return rgb, segs
 
 
 def bfs(offsets, adj, src):

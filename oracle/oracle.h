@@ -96,6 +96,35 @@ double orc_mutex_run(int32_t mode, int64_t T, int64_t K, const uint64_t* sched, 
  * Returns the number of reached vertices. */
 int64_t orc_bfs(int64_t n, const uint64_t* offsets, const uint32_t* adj, uint32_t src, uint32_t* dist);
 
+/* Sequential CPU ray tracer (Section V-B wavefront ray tracing computes the
+ * same per-pixel radiance; the queue only schedules the ray segments).
+ * Scene and camera as read from the workload description: spheres with
+ * Lambertian albedo, pinhole camera at cam looking along +z (image plane
+ * x = (2 (px + 0.5) / W - 1) * scale_x, y = (1 - 2 (py + 0.5) / H) * scale_y,
+ * z = 1), one sample at each pixel centre, sky radiance
+ * (1 - s) + s * (0.5, 0.7, 1.0) with s = (d.y + 1) / 2 on a miss, at most
+ * max_bounces scatterings (a hit after the last scattering contributes 0).
+ * Scattering direction normalize(n + p), p uniform in the unit ball by
+ * rejection from [-1, 1]^3 with 24-bit uniforms
+ * u = (splitmix64(seed, ((pixel * 16 + bounce) * 64 + attempt) * 4 + axis) >> 40) * 2^-24,
+ * at most 32 attempts (else p = 0); normalize falls back to n when
+ * |n + p|^2 <= 1e-12.  Nearest hit with t > 1e-4; equal t: lower sphere id.
+ * fp32 throughout, no fused multiply-add, IEEE division and square root. */
+typedef struct {
+    int32_t width, height, max_bounces, nspheres;
+    float cam_x, cam_y, cam_z, scale_x, scale_y;
+    uint64_t seed;
+    const float* centre;   /* nspheres x 3 */
+    const float* radius;   /* nspheres */
+    const float* albedo;   /* nspheres x 3 */
+} orc_rt_scene;
+
+/* Radiance of the m listed pixels (index py * width + px) into rgb[3 m];
+ * segments[m] (nullable) receives the number of traced segments per pixel.
+ * Uses `threads` host threads. */
+void orc_render_pixels(const orc_rt_scene* scene, const int64_t* pixels, int64_t m, float* rgb,
+                       int32_t* segments, int32_t threads);
+
 #ifdef __cplusplus
 }
 #endif

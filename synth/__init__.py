@@ -210,6 +210,13 @@ def bfs_sources(offsets: np.ndarray, seed: int, count: int = 3) -> np.ndarray:
 # Ray-tracing scene: spheres in the unit box
 # ---------------------------------------------------------------------------
 
+def camera_scale(width: int, height: int, vfov_deg: float = 40.0) -> tuple[float, float]:
+    """Image-plane half extents of a pinhole camera at distance 1: (tan(vfov/2) * W/H, tan(vfov/2)),
+    rounded to float32 once so that every consumer uses the same two numbers."""
+    t = np.tan(np.radians(vfov_deg) / 2.0)
+    return float(np.float32(t * width / height)), float(np.float32(t))
+
+
 def sphere_scene(count: int, seed: int = 0, mu: float = -4.0, sigma: float = 0.5) -> dict:
     """``count`` spheres, centres uniform in [0,1]^3, radii exp(N(mu, sigma)), albedo uniform in [0.2, 0.8]^3.
 
