@@ -43,6 +43,47 @@ extern "C" {
 int gq_bfs(gq_handle q_a, gq_handle q_b, uint64_t n, const uint64_t* d_offsets, const uint32_t* d_adj,
            uint32_t src, uint32_t* d_dist, unsigned long long* d_stats, void* stream);
 
+/* Tile-based wavefront ray tracing (Section V-B "Tile-based wavefront Ray
+ * Tracing"): the W x H image is split into tiles_x x tiles_y tiles, each with
+ * its own queue.  Primary rays are generated and enqueued per tile (the queue
+ * item is the pixel index; the ray state lives in the workspace), then a
+ * persistent kernel repeatedly dequeues a ray, traces one segment against all
+ * spheres, shades it, and re-enqueues the scattered ray into the same tile's
+ * queue, until a device work counter reaches zero.
+ * Scene model (the same as the oracle's tracer): spheres with Lambertian
+ * albedo; pinhole camera at cam looking along +z with image-plane half extents
+ * scale_x, scale_y at distance 1; one sample per pixel centre; sky radiance
+ * (1 - s) + s * (0.5, 0.7, 1.0), s = (d.y + 1) / 2, on a miss; at most
+ * max_bounces scatterings; scattering direction normalize(n + p), p uniform in
+ * the unit ball from a SplitMix64 stream keyed by (pixel, bounce, attempt).
+ * fp32 without fused multiply-add, IEEE division and square root. */
+typedef struct {
+    uint32_t width, height, tiles_x, tiles_y, max_bounces, nspheres;
+    float cam_x, cam_y, cam_z, scale_x, scale_y;
+    uint32_t reserved;
+    uint64_t seed;
+    const float* d_centre;   /* nspheres x 3 (device) */
+    const float* d_radius;   /* nspheres */
+    const float* d_albedo;   /* nspheres x 3 */
+} gq_rt_scene;
+
+/* Device workspace gq_render needs (ray state, per-tile counters). */
+int gq_render_workspace_bytes(const gq_rt_scene* scene, uint64_t* bytes);
+
+/* Renders the scene into d_image (height x width x 3 float, row-major).
+ *   tiles: host array of tiles_x * tiles_y queue handles of one kind, 4-byte
+ *     elements, each of capacity >= the pixels of one tile (G-WFQ-YMC: pool
+ *     cells >= that tile's segments, at most (max_bounces + 1) x its pixels),
+ *     and max_threads >= the threads gq_render launches (it uses at most
+ *     min(max_threads, resident threads)).  They are left empty.
+ *   nspheres <= 8192 (the spheres are staged in shared memory).
+ *   d_stats (nullable, 4 x uint64): segments traced, pixels finished, error
+ *     flags (bit 0 idle wait expired, bit 1 a reserved dequeue found the queue
+ *     empty), tiles.
+ * Errors: GQ_ERR_INVALID, GQ_ERR_CUDA. */
+int gq_render(const gq_handle* tiles, const gq_rt_scene* scene, void* d_workspace, float* d_image,
+              unsigned long long* d_stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

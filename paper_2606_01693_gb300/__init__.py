@@ -35,7 +35,7 @@ EXPORTS = [
     "gq_workspace_bytes", "gq_create", "gq_destroy", "gq_reset", "gq_enqueue_batch", "gq_dequeue_batch",
     "gq_sync_status", "gq_device_view", "gq_info", "gq_status_str", "gq_get_stats",
     "gq_run", "gq_run_sequence", "gq_drain", "gq_atomic_peak", "gq_fifo_static_roundtrip",
-    "gq_bfs",
+    "gq_bfs", "gq_render_workspace_bytes", "gq_render",
 ]
 
 
@@ -93,6 +93,8 @@ def load() -> ctypes.CDLL:
         "gq_atomic_peak": [i32, u32, u32, u32, P, u64, P, P],
         "gq_fifo_static_roundtrip": [P, u64, P, P, P],
         "gq_bfs": [P, P, u64, P, P, u32, P, P, P],
+        "gq_render_workspace_bytes": [P, P],
+        "gq_render": [P, P, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -225,6 +227,64 @@ def gq_bfs(q_a: int, q_b: int, offsets, adj, src: int, dist, stats=None, stream=
     """Level-synchronous BFS with two alternating frontier queues (4-byte queues of one kind)."""
     _check(load().gq_bfs(q_a, q_b, offsets.numel() - 1, _ptr(offsets), _ptr(adj), src, _ptr(dist), _ptr(stats),
                          _stream(stream)), "gq_bfs")
+
+
+class gq_rt_scene(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32), ("tiles_x", ctypes.c_uint32),
+                ("tiles_y", ctypes.c_uint32), ("max_bounces", ctypes.c_uint32), ("nspheres", ctypes.c_uint32),
+                ("cam_x", ctypes.c_float), ("cam_y", ctypes.c_float), ("cam_z", ctypes.c_float),
+                ("scale_x", ctypes.c_float), ("scale_y", ctypes.c_float), ("reserved", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("d_centre", ctypes.c_void_p), ("d_radius", ctypes.c_void_p),
+                ("d_albedo", ctypes.c_void_p)]
+
+
+def gq_render_workspace_bytes(scene: gq_rt_scene) -> int:
+    out = ctypes.c_uint64(0)
+    _check(load().gq_render_workspace_bytes(ctypes.byref(scene), ctypes.byref(out)), "gq_render_workspace_bytes")
+    return out.value
+
+
+def gq_render(tiles, scene: gq_rt_scene, workspace, image, stats=None, stream=None) -> None:
+    """Tile-based wavefront ray tracing; tiles: list of queue handles (tiles_x * tiles_y)."""
+    arr = (ctypes.c_void_p * len(tiles))(*tiles)
+    _check(load().gq_render(arr, ctypes.byref(scene), _ptr(workspace), _ptr(image), _ptr(stats), _stream(stream)),
+           "gq_render")
+
+
+class Renderer:
+    """Tile queues, workspace and scene arrays for gq_render (device memory from torch)."""
+
+    def __init__(self, kind, scene: dict, width: int, height: int, tiles=(8, 8), max_bounces=8, seed=0,
+                 max_threads=1 << 19):
+        import math
+        import torch
+        self.torch = torch
+        self.centre = torch.as_tensor(scene["centre"], dtype=torch.float32).reshape(-1).contiguous().cuda()
+        self.radius = torch.as_tensor(scene["radius"], dtype=torch.float32).contiguous().cuda()
+        self.albedo = torch.as_tensor(scene["albedo"], dtype=torch.float32).reshape(-1).contiguous().cuda()
+        cam = scene.get("camera", (0.5, 0.5, -1.5))
+        sx, sy = scene["scale"]
+        ns = self.radius.numel()
+        self.scene = gq_rt_scene(width, height, tiles[0], tiles[1], max_bounces, ns, cam[0], cam[1], cam[2], sx, sy, 0,
+                                 seed, self.centre.data_ptr() if ns else None, self.radius.data_ptr() if ns else None,
+                                 self.albedo.data_ptr() if ns else None)
+        tw, th = -(-width // tiles[0]), -(-height // tiles[1])
+        per_tile = tw * th
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        if k == GQ_YMC:
+            cap = (max_bounces + 1) * per_tile + (1 << 14)
+        else:
+            cap = 1 << max(12, (per_tile - 1).bit_length())
+        self.queues = [Queue(k, cap, 4, max_threads) for _ in range(tiles[0] * tiles[1])]
+        self.ws = torch.empty(gq_render_workspace_bytes(self.scene), dtype=torch.uint8, device="cuda")
+        self.image = torch.zeros((height, width, 3), dtype=torch.float32, device="cuda")
+        self.stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+
+    def render(self, stream=None):
+        for q in self.queues:
+            q.reset(stream)
+        gq_render([q.handle for q in self.queues], self.scene, self.ws, self.image, self.stats, stream)
+        return self.image
 
 
 # ---------------------------------------------------------------------------

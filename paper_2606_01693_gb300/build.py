@@ -16,7 +16,9 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgq.so")
-SOURCES = ["gq_api.cu", "gq_drivers.cu", "gq_peaks.cu", "gq_static.cu", "gq_apps.cu"]
+SOURCES = ["gq_api.cu", "gq_drivers.cu", "gq_peaks.cu", "gq_static.cu", "gq_apps.cu", "gq_rt.cu"]
+# per-file flags: the ray tracer's radiance must round like the sequential CPU trace
+EXTRA = {"gq_rt.cu": ["-fmad=false", "-prec-div=true", "-prec-sqrt=true", "-ftz=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc] + common + EXTRA.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
