@@ -26,7 +26,7 @@ using namespace gqd;
 namespace {
 
 constexpr u32 kMaxSpheres = 8192;
-constexpr u32 kIdleLimit = 1u << 26;
+constexpr u32 kIdleLimit = 1u << 24;
 
 struct RtWs {            // device workspace layout (byte offsets)
     u64 devs, pending, ctl, state, total;
