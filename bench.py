@@ -122,9 +122,10 @@ def cpu_baseline(T, K, seed, cpu_threads):
 
 
 def bench_apps(gq, synth, kinds, dev, reps=3):
-    """Level-synchronous BFS over two frontier queues of each kind (untimed for
-    the headline): R-MAT scale 22 (edge factor 16) from vertex 0 and the
-    4096 x 4096 grid from its corner; ms per search and scanned edges per second."""
+    """Applications on each queue kind, outside the headline step: level-synchronous
+    BFS over two frontier queues (R-MAT scale 22 from vertex 0, 4096 x 4096 grid
+    from its corner; ms and scanned edges per second) and tile-queue wavefront
+    ray tracing (MRays/s = traced segments per second)."""
     import torch
     out = {}
     graphs = {"rmat22": synth.rmat_csr_fast(22, seed=0), "grid4096": synth.grid_csr(4096, 4096)}
@@ -161,6 +162,36 @@ def bench_apps(gq, synth, kinds, dev, reps=3):
                                               "gteps": round(float(st[2]) / (t * 1e-3) / 1e9, 3)}
             qa.close()
             qb.close()
+    # wavefront ray tracing: 1920 x 1080, 4096 spheres, <= 8 bounces, 8 x 8 tile queues
+    W, H = 1920, 1080
+    sc = synth.sphere_scene(4096, seed=0)
+    sc["scale"] = synth.camera_scale(W, H)
+    props = torch.cuda.get_device_properties(dev)
+    for k in kinds:
+        r = gq.Renderer(k, sc, W, H, tiles=(8, 8), max_bounces=8)
+        r.render()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r.render()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = r.stats.cpu().numpy()
+        assert st[2] == 0 and st[1] == W * H
+        t = float(np.median(ms))
+        segs = int(st[0])
+        # ALU roofline: 17 fp32 operations per ray-sphere test (no fused multiply-add),
+        # one test per sphere per segment; peak = SMs x 128 fp32 lanes x max SM clock
+        flops = segs * 4096 * 17
+        peak = props.multi_processor_count * 128 * 2.07e9
+        out["rt_1920x1080_%s" % k] = {"ms": round(t, 3), "segments": segs, "mrays_s": round(segs / (t * 1e-3) / 1e6, 1),
+                                      "alu_tops": round(flops / (t * 1e-3) / 1e12, 2),
+                                      "alu_frac_of_peak": round(flops / (t * 1e-3) / peak, 3)}
+        for q in r.queues:
+            q.close()
     return out
 
 
