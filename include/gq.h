@@ -76,6 +76,10 @@ typedef struct {
      * (a power of two, 1..32); each group reserves its tickets with one
      * fetch-and-add.  Default 32 (the whole warp, Algorithm 1). */
     uint32_t batch_width;
+    /* Back-off: a ring operation whose ticket attempt failed sleeps this many
+     * nanoseconds (__nanosleep) before taking the next ticket.  Default 0. */
+    uint32_t backoff_ns;
+    uint32_t reserved_opt;
     /* Initial value of every ticket counter (tests of counter wrap-around).
      * Must be a multiple of 2 * capacity.  Default 0. */
     uint64_t start_ticket;
@@ -101,6 +105,8 @@ typedef struct {
     uint32_t patience_enq, patience_deq, help_delay;
     uint32_t batch_width;           /* WaveFAA group width                          */
     uint32_t ring_order;            /* log2(2n)                                    */
+    uint32_t backoff_ns;            /* sleep after a failed ticket attempt          */
+    uint32_t reserved1;
     uint64_t capacity;              /* ring: n; YMC: pool cells                    */
     uint64_t slot_mask;             /* 2n - 1                                      */
     uint64_t cycle_mask;            /* R - 1, R = 2^cycle_bits                     */

@@ -44,6 +44,8 @@ extern "C" {
 
 enum { GQ_RUN_PAIRS = 0, GQ_RUN_MIXED = 1, GQ_RUN_SPLIT = 2 };
 
+#define GQ_VIEW_BYTES 512   /* upper bound of sizeof(gq_dev) */
+
 /* Counter slots accumulated (atomically added) by gq_run into d_counts[8]. */
 enum {
     GQ_CNT_ENQ_OK = 0, GQ_CNT_ENQ_FULL = 1, GQ_CNT_DEQ_OK = 2, GQ_CNT_DEQ_EMPTY = 3,
@@ -99,6 +101,37 @@ enum {
 int gq_atomic_peak(int pattern, uint32_t blocks, uint32_t threads, uint32_t iters,
                    unsigned long long* d_buf, uint64_t buf_words, unsigned long long* d_sink,
                    void* stream);
+
+/* ---- many independent queues in one persistent launch (batched form) ----
+ *
+ * gq_multi_prepare copies the device views of Q queues (same kind and element
+ * size) into d_views (Q * sizeof(gq_dev) bytes of device memory; sizeof(gq_dev)
+ * never exceeds GQ_VIEW_BYTES).  `tune`
+ * (nullable) overrides the WaveFAA batch width and the back-off of every copied
+ * view (0 fields keep the queue's own), which is how the autotuner tries
+ * settings without recreating queues.  Asynchronous on `stream`. */
+int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void* d_views, const gq_options* tune,
+                     void* stream);
+
+typedef struct {
+    uint32_t nqueues;
+    uint32_t threads_per_queue;    /* logical threads of each queue, multiple of 32       */
+    uint32_t producers_per_queue;  /* the first this many of each queue's threads enqueue */
+    uint32_t block;                /* threads per block, multiple of 32                    */
+    uint32_t blocks;               /* grid size; 0 = every resident block                  */
+    uint32_t kind, elem_bytes;     /* must match the views                                 */
+    uint32_t reserved;
+    uint64_t ops_per_queue;        /* split evenly over the queue's threads                */
+    unsigned long long* d_counts;  /* 8 words, added to (GQ_CNT_* layout)                  */
+} gq_multi_args;
+
+/* Producer/consumer split workload on every queue of d_views at once: logical
+ * thread t of queue q enqueues tokens ((q * threads_per_queue + t) << 32) |
+ * (seq + 1) if t < producers_per_queue, else dequeues; ops_per_queue split
+ * evenly.  A persistent grid strides over the logical threads; each logical
+ * thread runs its operations in order and uses record id t in queue q.
+ * Errors: GQ_ERR_INVALID, GQ_ERR_CUDA. */
+int gq_run_multi(const void* d_views, const gq_multi_args* args, void* stream);
 
 #ifdef __cplusplus
 }

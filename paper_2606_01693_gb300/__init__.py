@@ -35,8 +35,9 @@ EXPORTS = [
     "gq_workspace_bytes", "gq_create", "gq_destroy", "gq_reset", "gq_enqueue_batch", "gq_dequeue_batch",
     "gq_sync_status", "gq_device_view", "gq_info", "gq_status_str", "gq_get_stats",
     "gq_run", "gq_run_sequence", "gq_drain", "gq_atomic_peak", "gq_fifo_static_roundtrip",
-    "gq_bfs", "gq_render_workspace_bytes", "gq_render",
+    "gq_bfs", "gq_render_workspace_bytes", "gq_render", "gq_multi_prepare", "gq_run_multi",
 ]
+GQ_VIEW_BYTES = 512
 
 
 class GqError(RuntimeError):
@@ -49,6 +50,7 @@ class gq_options(ctypes.Structure):
     _fields_ = [("cycle_bits", ctypes.c_uint32), ("patience_enq", ctypes.c_uint32),
                 ("patience_deq", ctypes.c_uint32), ("patience_set", ctypes.c_uint32),
                 ("help_delay", ctypes.c_uint32), ("batch_width", ctypes.c_uint32),
+                ("backoff_ns", ctypes.c_uint32), ("reserved_opt", ctypes.c_uint32),
                 ("start_ticket", ctypes.c_uint64)]
 
 
@@ -95,6 +97,8 @@ def load() -> ctypes.CDLL:
         "gq_bfs": [P, P, u64, P, P, u32, P, P, P],
         "gq_render_workspace_bytes": [P, P],
         "gq_render": [P, P, P, P, P, P],
+        "gq_multi_prepare": [P, u32, P, P, P],
+        "gq_run_multi": [P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -227,6 +231,63 @@ def gq_bfs(q_a: int, q_b: int, offsets, adj, src: int, dist, stats=None, stream=
     """Level-synchronous BFS with two alternating frontier queues (4-byte queues of one kind)."""
     _check(load().gq_bfs(q_a, q_b, offsets.numel() - 1, _ptr(offsets), _ptr(adj), src, _ptr(dist), _ptr(stats),
                          _stream(stream)), "gq_bfs")
+
+
+class gq_multi_args(ctypes.Structure):
+    _fields_ = [("nqueues", ctypes.c_uint32), ("threads_per_queue", ctypes.c_uint32),
+                ("producers_per_queue", ctypes.c_uint32), ("block", ctypes.c_uint32), ("blocks", ctypes.c_uint32),
+                ("kind", ctypes.c_uint32), ("elem_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("ops_per_queue", ctypes.c_uint64), ("d_counts", ctypes.c_void_p)]
+
+
+def gq_multi_prepare(handles, views, tune: gq_options | None = None, stream=None) -> None:
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    _check(load().gq_multi_prepare(arr, len(handles), _ptr(views), ctypes.byref(tune) if tune else None,
+                                   _stream(stream)), "gq_multi_prepare")
+
+
+def gq_run_multi(views, nqueues: int, kind: int, elem_bytes: int, threads_per_queue: int, producers_per_queue: int,
+                 ops_per_queue: int, counts, block: int = 256, blocks: int = 0, stream=None) -> None:
+    a = gq_multi_args(nqueues, threads_per_queue, producers_per_queue, block, blocks, kind, elem_bytes, 0,
+                      ops_per_queue, _ptr(counts))
+    _check(load().gq_run_multi(_ptr(views), ctypes.byref(a), _stream(stream)), "gq_run_multi")
+
+
+class MultiQueue:
+    """Q independent queues of one kind, for the batched persistent driver."""
+
+    def __init__(self, kind, capacities, elem_bytes: int = 8, max_threads: int = 1024, **options):
+        import torch
+        self.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+        self.elem_bytes = elem_bytes
+        self.queues = [Queue(self.kind, int(c), elem_bytes, max_threads, **options) for c in capacities]
+        self.handles = [q.handle for q in self.queues]
+        self.views = torch.empty(len(self.queues) * GQ_VIEW_BYTES, dtype=torch.uint8, device="cuda")
+        self.prepare()
+
+    def prepare(self, batch_width: int = 0, backoff_ns: int | None = None, stream=None):
+        tune = None
+        if batch_width or backoff_ns is not None:
+            tune = gq_options(batch_width=batch_width, backoff_ns=backoff_ns or 0)
+        gq_multi_prepare(self.handles, self.views, tune, stream)
+
+    def reset(self, stream=None):
+        for q in self.queues:
+            q.reset(stream)
+
+    def run(self, threads_per_queue, producers_per_queue, ops_per_queue, counts, block=256, blocks=0, stream=None):
+        gq_run_multi(self.views, len(self.queues), self.kind, self.elem_bytes, threads_per_queue, producers_per_queue,
+                     ops_per_queue, counts, block, blocks, stream)
+
+    def run_per_call(self, threads_per_queue, producers_per_queue, ops_per_queue, counts, block=256, stream=None):
+        """The plain form: one split-workload launch per queue, one after another."""
+        for q in self.queues:
+            gq_run(q.handle, GQ_RUN_SPLIT, threads_per_queue, block=block, producers=producers_per_queue,
+                   total_ops=ops_per_queue, counts=counts, stream=stream)
+
+    def close(self):
+        for q in self.queues:
+            q.close()
 
 
 class gq_rt_scene(ctypes.Structure):

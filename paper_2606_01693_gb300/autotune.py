@@ -1,0 +1,84 @@
+"""Autotuner for the batched persistent queue driver.
+
+Tries WaveFAA batch widths, blocks per SM and back-off delays on the caller's
+workload (CUDA-event timing of the run kernel, median of `reps`), keeps the
+fastest, and caches the choice per GPU, queue kind and workload shape in a JSON
+file (``$GQ_AUTOTUNE_CACHE`` or ``~/.cache/gq_autotune.json``).
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+
+def _cache_path() -> str:
+    return os.environ.get("GQ_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "gq_autotune.json"))
+
+
+def _load_cache() -> dict:
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save_cache(c: dict) -> None:
+    p = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        tmp = p + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(c, f, indent=1, sort_keys=True)
+        os.replace(tmp, p)
+    except OSError:
+        pass
+
+
+def tune_multi(mq, threads_per_queue: int, producers_per_queue: int, ops_per_queue: int,
+               widths=(32, 16, 8, 4, 1), blocks_per_sm=(0, 2, 4, 8), backoffs=(0, 100, 400), reps: int = 3,
+               use_cache: bool = True, block: int = 256) -> dict:
+    """Returns {"batch_width", "blocks", "backoff_ns", "mops", "table"} for MultiQueue `mq`
+    and leaves `mq` prepared with the winning settings."""
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    key = "%s|kind%d|q%d|tpq%d|ppq%d|opq%d|cap%d" % (props.name, mq.kind, len(mq.queues), threads_per_queue,
+                                                     producers_per_queue, ops_per_queue,
+                                                     int(sum(q.capacity for q in mq.queues)))
+    cache = _load_cache() if use_cache else {}
+    if use_cache and key in cache:
+        best = cache[key]
+        mq.prepare(batch_width=best["batch_width"], backoff_ns=best["backoff_ns"])
+        return dict(best, cached=True)
+    counts = torch.zeros(8, dtype=torch.int64, device="cuda")
+    table = []
+    for w in widths:
+        for bo in backoffs:
+            mq.prepare(batch_width=w, backoff_ns=bo)
+            for bps in blocks_per_sm:
+                blocks = bps * props.multi_processor_count
+                ms = []
+                for r in range(reps + 1):
+                    mq.reset()
+                    counts.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    mq.run(threads_per_queue, producers_per_queue, ops_per_queue, counts, block=block, blocks=blocks)
+                    e1.record()
+                    e1.synchronize()
+                    if r:
+                        ms.append(e0.elapsed_time(e1))
+                c = counts.cpu().numpy()
+                mops = float(c[0] + c[2]) / (float(np.median(ms)) * 1e-3) / 1e6
+                table.append({"batch_width": w, "backoff_ns": bo, "blocks": blocks, "mops": round(mops, 1)})
+    best = max(table, key=lambda r: r["mops"])
+    mq.prepare(batch_width=best["batch_width"], backoff_ns=best["backoff_ns"])
+    out = dict(best)
+    if use_cache:
+        cache[key] = out
+        _save_cache(cache)
+    out["table"] = table
+    out["cached"] = False
+    return out

@@ -32,6 +32,7 @@ int resolve(int kind, uint64_t cap, uint32_t elem, uint32_t max_threads, const g
     if (in) o = *in;
     if (o.batch_width == 0) o.batch_width = 32;
     if (!is_pow2(o.batch_width) || o.batch_width > 32) return GQ_ERR_INVALID;
+    if (o.backoff_ns > 1000000) return GQ_ERR_INVALID;
     if (kind == GQ_YMC) {
         if (cap < 2 || cap > (1ull << 40)) return GQ_ERR_INVALID;
         if (max_threads > (1u << 24) - 1) return GQ_ERR_TOO_MANY_THREADS;   // 24-bit thread field of cell references
@@ -322,6 +323,7 @@ extern "C" int gq_create(int kind, uint64_t capacity, uint32_t elem_bytes, uint3
     d.patience_deq = o.patience_deq;
     d.help_delay = o.help_delay;
     d.batch_width = o.batch_width;
+    d.backoff_ns = o.backoff_ns;
     d.capacity = capacity;
     if (kind != GQ_YMC) {
         d.ring_order = d.log2n + 1;

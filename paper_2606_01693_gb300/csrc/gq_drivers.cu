@@ -8,6 +8,8 @@
 
 using namespace gqd;
 
+static_assert(sizeof(gq_dev) <= GQ_VIEW_BYTES, "gq_dev must fit GQ_VIEW_BYTES");
+
 namespace {
 
 struct RunK {
@@ -157,7 +159,121 @@ int dispatch_drain(gq_queue* h, u64* out, u64 max, unsigned long long* count, cu
     return gq_check_launch();
 }
 
+struct MultiK {
+    u32 nq, tpq, ppq;
+    u64 opq;
+    unsigned long long* counts;
+};
+
+template <class T, int KIND>
+__global__ void __launch_bounds__(256, 4) k_run_multi(const gq_dev* __restrict__ views, const __grid_constant__ MultiK a) {
+    const u64 total = (u64)a.nq * a.tpq;
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    u32 c_enq_ok = 0, c_full = 0, c_deq_ok = 0, c_empty = 0, c_err = 0;
+    u64 s_enq = 0, s_deq = 0;
+    for (u64 L = (u64)blockIdx.x * blockDim.x + threadIdx.x; L < total; L += stride) {
+        const u32 qi = (u32)(L / a.tpq), t = (u32)(L % a.tpq);
+        const gq_dev& q = views[qi];
+        const u32 nops = (u32)(a.opq / a.tpq) + (t < (u32)(a.opq % a.tpq) ? 1u : 0u);
+        if (t < a.ppq) {
+            for (u32 i = 0; i < nops; ++i) {
+                const u64 v = (sizeof(T) == 4) ? ((L << 16) | i) : ((L << 32) | (u64)(i + 1));
+                const int s = queue_enqueue<T, KIND>(q, (T)v, t);
+                if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
+                else if (s == GQ_FULL) ++c_full;
+                else ++c_err;
+            }
+        } else {
+            for (u32 i = 0; i < nops; ++i) {
+                T x = 0;
+                const int s = queue_dequeue<T, KIND>(q, &x, t);
+                if (s == GQ_OK) { ++c_deq_ok; s_deq += (u64)x; }
+                else if (s == GQ_EMPTY) ++c_empty;
+                else ++c_err;
+            }
+        }
+    }
+    warp_add_full(&a.counts[GQ_CNT_ENQ_OK], c_enq_ok);
+    warp_add_full(&a.counts[GQ_CNT_ENQ_FULL], c_full);
+    warp_add_full(&a.counts[GQ_CNT_DEQ_OK], c_deq_ok);
+    warp_add_full(&a.counts[GQ_CNT_DEQ_EMPTY], c_empty);
+    warp_add_full(&a.counts[GQ_CNT_SUM_ENQ], s_enq);
+    warp_add_full(&a.counts[GQ_CNT_SUM_DEQ], s_deq);
+    warp_add_full(&a.counts[GQ_CNT_ERRORS], c_err);
+}
+
+template <class T, int KIND>
+int launch_multi(const gq_dev* views, const gq_multi_args& g, cudaStream_t st) {
+    MultiK a{g.nqueues, g.threads_per_queue, g.producers_per_queue, g.ops_per_queue, g.d_counts};
+    uint32_t blocks = g.blocks;
+    const uint64_t need = ((uint64_t)g.nqueues * g.threads_per_queue + g.block - 1) / g.block;
+    if (blocks == 0) {
+        int dev = 0, sms = 0, occ = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_run_multi<T, KIND>, (int)g.block, 0) != cudaSuccess)
+            return GQ_ERR_CUDA;
+        blocks = (uint32_t)(occ > 0 ? occ : 1) * (uint32_t)sms;
+    }
+    if (blocks > need) blocks = (uint32_t)need;
+    k_run_multi<T, KIND><<<blocks, g.block, 0, st>>>(views, a);
+    return gq_check_launch();
+}
+
+__global__ void k_multi_tune(gq_dev* views, u32 n, u32 width, u32 backoff, u32 set_backoff) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (width) views[i].batch_width = width;
+    if (set_backoff) views[i].backoff_ns = backoff;
+}
+
 }  // namespace
+
+extern "C" int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void* d_views, const gq_options* tune,
+                                void* stream) {
+    if (!queues || !nqueues || !d_views) return GQ_ERR_INVALID;
+    for (uint32_t i = 0; i < nqueues; ++i)
+        if (!queues[i] || queues[i]->dev.kind != queues[0]->dev.kind ||
+            queues[i]->dev.elem_bytes != queues[0]->dev.elem_bytes || queues[i]->device != queues[0]->device)
+            return GQ_ERR_INVALID;
+    if (tune && tune->batch_width && (tune->batch_width > 32 || (tune->batch_width & (tune->batch_width - 1))))
+        return GQ_ERR_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    gq_dev* v = static_cast<gq_dev*>(d_views);
+    for (uint32_t i = 0; i < nqueues; ++i)
+        if (cudaMemcpyAsync(v + i, &queues[i]->dev, sizeof(gq_dev), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return GQ_ERR_CUDA;
+    if (tune) {
+        k_multi_tune<<<(nqueues + 255) / 256, 256, 0, st>>>(v, nqueues, tune->batch_width, tune->backoff_ns, 1);
+        return gq_check_launch();
+    }
+    return GQ_OK;
+}
+
+extern "C" int gq_run_multi(const void* d_views, const gq_multi_args* args, void* stream) {
+    if (!d_views || !args || !args->d_counts || !args->nqueues) return GQ_ERR_INVALID;
+    const gq_multi_args& g = *args;
+    if (g.threads_per_queue == 0 || (g.threads_per_queue & 31) || g.block == 0 || g.block > 1024 || (g.block & 31) ||
+        g.producers_per_queue > g.threads_per_queue || g.kind > GQ_YMC || (g.elem_bytes != 4 && g.elem_bytes != 8))
+        return GQ_ERR_INVALID;
+    if (g.elem_bytes == 4 && ((uint64_t)g.nqueues * g.threads_per_queue > 65536 ||
+                              g.ops_per_queue / g.threads_per_queue >= 65536))
+        return GQ_ERR_INVALID;
+    const gq_dev* v = static_cast<const gq_dev*>(d_views);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (g.elem_bytes == 4) {
+        switch (g.kind) {
+            case GQ_LFQ: return launch_multi<unsigned int, GQ_LFQ>(v, g, st);
+            case GQ_WFQ: return launch_multi<unsigned int, GQ_WFQ>(v, g, st);
+            default: return launch_multi<unsigned int, GQ_YMC>(v, g, st);
+        }
+    }
+    switch (g.kind) {
+        case GQ_LFQ: return launch_multi<unsigned long long, GQ_LFQ>(v, g, st);
+        case GQ_WFQ: return launch_multi<unsigned long long, GQ_WFQ>(v, g, st);
+        default: return launch_multi<unsigned long long, GQ_YMC>(v, g, st);
+    }
+}
 
 extern "C" int gq_run(gq_handle h, const gq_run_args* args, void* stream) {
     if (!h || !args || !args->d_counts) return GQ_ERR_INVALID;

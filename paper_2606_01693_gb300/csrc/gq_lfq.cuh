@@ -103,6 +103,7 @@ __device__ int lfq_ring_enq(const gq_dev& q, const gq_ring_view& r, u32 idx) {
             if (ld_rlx(r.threshold) != q.thr_reset) thr_reset(r.threshold, q.thr_reset, q.err);
             return GQ_OK;
         }
+        if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
     latch_error(q.err, GQ_ERR_TIMEOUT);
     return GQ_ERR_TIMEOUT;
@@ -144,6 +145,7 @@ __device__ int lfq_ring_deq(const gq_dev& q, const gq_ring_view& r, u32* idx) {
             return GQ_EMPTY;
         }
         if (thr_dec(r.threshold) <= 0) return GQ_EMPTY;
+        if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
     latch_error(q.err, GQ_ERR_TIMEOUT);
     return GQ_ERR_TIMEOUT;

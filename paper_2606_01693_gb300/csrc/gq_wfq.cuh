@@ -458,8 +458,10 @@ template <bool MATCH>
 __device__ int wfq_ring_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u32 me, u32 patience) {
     wfq_maybe_help(R, q, me);
     u64 t = 0;
-    for (u32 p = 0; p < patience; ++p)
+    for (u32 p = 0; p < patience; ++p) {
         if (wfq_try_enq<MATCH>(R, q, idx, &t) == kTryOk) return GQ_OK;
+        if (q.backoff_ns) __nanosleep(q.backoff_ns);
+    }
     if (patience == 0) t = (g_cnt(ld_rlx(R.tail)) - 1) & kCntMask;   // a ticket value r never held
     const u64 l = wfq_slow_request(R, q, me, true, t, idx);
     if (!l) {
@@ -488,6 +490,7 @@ __device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u3
         const int s = wfq_try_deq<MATCH>(R, q, idx, &h);
         if (s == kTryOk) return GQ_OK;
         if (s == kTryEmpty) return GQ_EMPTY;
+        if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
     if (patience == 0) h = (g_cnt(ld_rlx(R.head)) - 1) & kCntMask;
     const u64 l = wfq_slow_request(R, q, me, false, h, 0);

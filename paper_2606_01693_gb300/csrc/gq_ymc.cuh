@@ -239,6 +239,7 @@ __device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid) {
         u64 b = kVBot;
         if (aref<u64>(q.cell_val[i]).compare_exchange_strong(b, x, kRel, kRlx)) return GQ_OK;
         id = i;
+        if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
     return ymc_enq_slow(q, tid, x, id);
 }
@@ -260,6 +261,7 @@ __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid) {
             if (!cas(q.cell_deq + i, b, kRefTop)) res = kYUnusable;   // a slow dequeue took it
         }
         id = i;
+        if (res == kYUnusable && q.backoff_ns) __nanosleep(q.backoff_ns);
     }
     if (res == kYUnusable) {
         // slow path: publish <id, idx = id> and help it to completion

@@ -1,0 +1,99 @@
+"""Batched form on the GPU (run with -m gpu): many independent queues in one
+persistent launch, also replayed from a captured CUDA graph, against the
+oracle's checks: per-queue FIFO order of what is left, exactly-once in the
+aggregate (checksums), and the same operation counts as the per-call form's
+bounds."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2606_01693_gb300 as gq
+import synth
+from paper_2606_01693_gb300 import autotune
+
+from gpu_util import DEV, drain
+
+pytestmark = pytest.mark.gpu
+KINDS = list(gq.READY_KINDS)
+
+
+def _caps(kind, Q, seed, ops_per_queue):
+    r = synth.splitmix64(seed, np.arange(Q)) >> np.uint64(40)
+    lg = 8 + (r.astype(np.float64) * 2.0**-24 * 9).astype(np.int64)      # log-uniform 2^8 .. 2^16
+    caps = (1 << lg)
+    if kind == "ymc":                                                       # pool: one cell per ticket
+        caps = np.full(Q, 3 * ops_per_queue + (1 << 12))
+    return caps
+
+
+def _check(mq, counts, Q, TPQ, PPQ, OPQ):
+    c = counts.cpu().numpy().view(np.uint64)
+    nops = synth.split_ops_per_thread(OPQ, TPQ)
+    assert c[0] + c[1] == Q * nops[:PPQ].sum()
+    assert c[2] + c[3] == Q * nops[PPQ:].sum()
+    assert c[6] == 0
+    left_sum = np.uint64(0)
+    for i, q in enumerate(mq.queues):
+        assert q.sync_status() == 0
+        left = drain(q, int(3 * OPQ + (1 << 16)))
+        rep = oracle.check_log(np.zeros((0, 1), np.uint8), np.zeros((0, 1), np.int8), np.zeros((0, 1), np.uint64),
+                               left)
+        assert rep["violations"] == 0, (i, str(rep))
+        assert len(np.unique(left)) == len(left)
+        assert ((left >> np.uint64(32)) // np.uint64(TPQ) == np.uint64(i)).all()     # no item crossed queues
+        with np.errstate(over="ignore"):
+            left_sum = left_sum + left.sum(dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        assert np.uint64(c[4]) == np.uint64(c[5]) + left_sum          # exactly once, aggregate
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("frac", [0.1, 0.5, 0.9])
+def test_persistent_multi_queue(kind, frac):
+    Q, TPQ, OPQ = 64, 256, 20000
+    PPQ = int(frac * TPQ)
+    mq = gq.MultiQueue(kind, _caps(kind, Q, 5, OPQ), 8, TPQ)
+    counts = torch.zeros(8, dtype=torch.int64, device=DEV)
+    mq.run(TPQ, PPQ, OPQ, counts)
+    _check(mq, counts, Q, TPQ, PPQ, OPQ)
+    mq.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_graph_replay_matches(kind):
+    Q, TPQ, OPQ, PPQ = 32, 256, 10000, 128
+    mq = gq.MultiQueue(kind, _caps(kind, Q, 9, OPQ), 8, TPQ)
+    counts = torch.zeros(8, dtype=torch.int64, device=DEV)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        mq.reset()
+        mq.run(TPQ, PPQ, OPQ, counts)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        mq.reset()
+        counts.zero_()
+        mq.run(TPQ, PPQ, OPQ, counts)
+    for _ in range(3):
+        g.replay()
+        torch.cuda.synchronize()
+        _check(mq, counts, Q, TPQ, PPQ, OPQ)
+    mq.close()
+
+
+def test_autotuner_picks_a_valid_setting(tmp_path, monkeypatch):
+    monkeypatch.setenv("GQ_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
+    Q, TPQ, OPQ, PPQ = 16, 256, 5000, 128
+    mq = gq.MultiQueue("lfq", _caps("lfq", Q, 3, OPQ), 8, TPQ)
+    best = autotune.tune_multi(mq, TPQ, PPQ, OPQ, widths=(32, 8), blocks_per_sm=(0, 2), backoffs=(0, 200), reps=1)
+    assert best["batch_width"] in (32, 8) and best["mops"] > 0 and len(best["table"]) == 8
+    again = autotune.tune_multi(mq, TPQ, PPQ, OPQ, widths=(32, 8), blocks_per_sm=(0, 2), backoffs=(0, 200), reps=1)
+    assert again["cached"] and again["batch_width"] == best["batch_width"]
+    counts = torch.zeros(8, dtype=torch.int64, device=DEV)
+    mq.reset()
+    mq.run(TPQ, PPQ, OPQ, counts, blocks=best["blocks"])
+    _check(mq, counts, Q, TPQ, PPQ, OPQ)
+    mq.close()
