@@ -7,7 +7,6 @@ import numpy as np
 import pytest
 import torch
 
-import oracle
 import paper_2606_01693_gb300 as gq
 import synth
 from paper_2606_01693_gb300 import autotune
@@ -37,9 +36,11 @@ def _check(mq, counts, Q, TPQ, PPQ, OPQ):
     for i, q in enumerate(mq.queues):
         assert q.sync_status() == 0
         left = drain(q, int(3 * OPQ + (1 << 16)))
-        rep = oracle.check_log(np.zeros((0, 1), np.uint8), np.zeros((0, 1), np.int8), np.zeros((0, 1), np.uint64),
-                               left)
-        assert rep["violations"] == 0, (i, str(rep))
+        # FIFO: what is left of each producer comes out of a single-thread drain in sequence order
+        prod, seq = left >> np.uint64(32), left & np.uint64(0xFFFFFFFF)
+        order = np.argsort(prod, kind="stable")
+        same = prod[order][1:] == prod[order][:-1]
+        assert (seq[order][1:][same] > seq[order][:-1][same]).all(), i
         assert len(np.unique(left)) == len(left)
         assert ((left >> np.uint64(32)) // np.uint64(TPQ) == np.uint64(i)).all()     # no item crossed queues
         with np.errstate(over="ignore"):
