@@ -43,6 +43,37 @@ extern "C" {
 int gq_bfs(gq_handle q_a, gq_handle q_b, uint64_t n, const uint64_t* d_offsets, const uint32_t* d_adj,
            uint32_t src, uint32_t* d_dist, unsigned long long* d_stats, void* stream);
 
+/* ---- batched BFS: many independent instances in one persistent launch ----
+ * Instances are distributed through a queue of instance ids; each thread-block
+ * cluster (cluster_blocks blocks of 256 threads, hardware cluster barrier
+ * between levels) takes the next id, runs a level-synchronous BFS on its own
+ * pair of frontier queues, and repeats until the id queue is empty. */
+typedef struct {
+    uint64_t n;                  /* vertices                          */
+    const uint64_t* d_offsets;   /* n + 1                              */
+    const uint32_t* d_adj;
+    uint32_t* d_dist;            /* n, written (GQ_BFS_UNREACHED)      */
+    uint32_t src;
+    uint32_t reserved;
+} gq_bfs_instance;
+
+/* Workspace for gq_bfs_batch with `slots` clusters. */
+int gq_bfs_batch_workspace_bytes(uint32_t slots, uint64_t* bytes);
+
+/* d_instances: device array of ninst gq_bfs_instance; d_order: device array of
+ * the ninst instance ids in the order they are handed out (largest first keeps
+ * the tail short).  id_queue: an empty 4-byte queue of capacity >= ninst with
+ * max_threads >= slots.  frontier: 2 * slots empty 4-byte queues of the same
+ * kind as each other, capacity >= the largest instance's vertices (G-WFQ-YMC:
+ * pool >= 3 n + 64 (levels + 1) of the largest instance: the cells used by an
+ * instance are cleared on the device before the next one), max_threads >=
+ * cluster_blocks * 256.  cluster_blocks in {1, 2, 4, 8}.  All queues are left
+ * empty.  d_stats (nullable, 4 x uint64): instances done, edges scanned,
+ * levels summed over instances, errors. */
+int gq_bfs_batch(gq_handle id_queue, const gq_handle* frontier, uint32_t slots, uint32_t cluster_blocks,
+                 const gq_bfs_instance* d_instances, const uint32_t* d_order, uint32_t ninst, void* d_workspace,
+                 unsigned long long* d_stats, void* stream);
+
 /* Tile-based wavefront ray tracing (Section V-B "Tile-based wavefront Ray
  * Tracing"): the W x H image is split into tiles_x x tiles_y tiles, each with
  * its own queue.  Primary rays are generated and enqueued per tile (the queue

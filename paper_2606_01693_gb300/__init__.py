@@ -36,6 +36,7 @@ EXPORTS = [
     "gq_sync_status", "gq_device_view", "gq_info", "gq_status_str", "gq_get_stats",
     "gq_run", "gq_run_sequence", "gq_drain", "gq_atomic_peak", "gq_fifo_static_roundtrip",
     "gq_bfs", "gq_render_workspace_bytes", "gq_render", "gq_multi_prepare", "gq_run_multi",
+    "gq_bfs_batch_workspace_bytes", "gq_bfs_batch",
 ]
 GQ_VIEW_BYTES = 512
 
@@ -99,6 +100,8 @@ def load() -> ctypes.CDLL:
         "gq_render": [P, P, P, P, P, P],
         "gq_multi_prepare": [P, u32, P, P, P],
         "gq_run_multi": [P, P, P],
+        "gq_bfs_batch_workspace_bytes": [u32, P],
+        "gq_bfs_batch": [P, P, u32, u32, P, P, u32, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -231,6 +234,55 @@ def gq_bfs(q_a: int, q_b: int, offsets, adj, src: int, dist, stats=None, stream=
     """Level-synchronous BFS with two alternating frontier queues (4-byte queues of one kind)."""
     _check(load().gq_bfs(q_a, q_b, offsets.numel() - 1, _ptr(offsets), _ptr(adj), src, _ptr(dist), _ptr(stats),
                          _stream(stream)), "gq_bfs")
+
+
+class gq_bfs_instance(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("d_offsets", ctypes.c_void_p), ("d_adj", ctypes.c_void_p),
+                ("d_dist", ctypes.c_void_p), ("src", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class BatchBfs:
+    """Many BFS instances in one persistent launch (one per thread-block cluster at a time)."""
+
+    def __init__(self, kind, graphs, sources, slots=64, cluster_blocks=4, max_levels=64):
+        import numpy as np
+        import torch
+        self.torch = torch
+        self.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+        self.graphs = []
+        inst = (gq_bfs_instance * len(graphs))()
+        nmax = 1
+        for i, ((off, adj), src) in enumerate(zip(graphs, sources)):
+            d_off = torch.from_numpy(off.view(np.int64)).cuda()
+            d_adj = torch.from_numpy(adj.view(np.int32)).cuda()
+            dist = torch.empty(len(off) - 1, dtype=torch.int32, device="cuda")
+            self.graphs.append((d_off, d_adj, dist))
+            inst[i] = gq_bfs_instance(len(off) - 1, d_off.data_ptr(), d_adj.data_ptr(), dist.data_ptr(), int(src), 0)
+            nmax = max(nmax, len(off) - 1)
+        self.ninst = len(graphs)
+        self.d_inst = torch.frombuffer(bytearray(bytes(inst)), dtype=torch.uint8).cuda()
+        sizes = np.array([len(g[0]) - 1 for g in graphs])
+        self.d_order = torch.from_numpy(np.argsort(-sizes, kind="stable").astype(np.int32)).cuda()
+        self.slots, self.cluster_blocks = slots, cluster_blocks
+        if self.kind == GQ_YMC:
+            cap = 3 * nmax + 64 * (max_levels + 1) + (1 << 17)
+        else:
+            cap = min(1 << max(12, (nmax - 1).bit_length()), 1 << 23)
+        self.idq = Queue(GQ_LFQ, 1 << max(1, (self.ninst - 1).bit_length()), 4, max(slots, 32))
+        self.frontier = [Queue(self.kind, cap, 4, cluster_blocks * 256) for _ in range(2 * slots)]
+        ws = ctypes.c_uint64(0)
+        _check(load().gq_bfs_batch_workspace_bytes(slots, ctypes.byref(ws)), "gq_bfs_batch_workspace_bytes")
+        self.ws = torch.empty(ws.value, dtype=torch.uint8, device="cuda")
+        self.stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+
+    def run(self, stream=None):
+        arr = (ctypes.c_void_p * len(self.frontier))(*[q.handle for q in self.frontier])
+        _check(load().gq_bfs_batch(self.idq.handle, arr, self.slots, self.cluster_blocks, _ptr(self.d_inst),
+                                   _ptr(self.d_order), self.ninst, _ptr(self.ws), _ptr(self.stats),
+                                   _stream(stream)), "gq_bfs_batch")
+
+    def dists(self):
+        return [g[2] for g in self.graphs]
 
 
 class gq_multi_args(ctypes.Structure):

@@ -10,7 +10,10 @@
 // warp with coalesced adjacency loads.  A neighbour is claimed with a CAS on
 // its distance word (UNREACHED -> level + 1); distances are unique, so any
 // claim order yields the same distances.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
+
+#include <vector>
 
 #include "../../include/gq_apps.h"
 #include "gq_host.h"
@@ -73,7 +76,6 @@ __global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, 
     const u32 nthreads = gridDim.x * blockDim.x;
     const u32 lane = threadIdx.x & 31;
     const u32 warp = tid >> 5;
-    const u32 nwarps = nthreads >> 5;
     for (u64 v = tid; v < n; v += nthreads) dist[v] = kUnreached;
     if (!grid_barrier(ctl, gridDim.x)) return;
     if (tid == 0) {
@@ -154,7 +156,201 @@ int launch_bfs(gq_handle ha, gq_handle hb, uint64_t n, const uint64_t* off, cons
     return gq_check_launch();
 }
 
+// ---------------------------------------------------------------------------
+// Batched BFS: one instance per thread-block cluster at a time
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+constexpr u32 kNoInstance = 0xFFFFFFFFu;
+
+struct BatchK {
+    const gq_bfs_instance* inst;
+    const u32* order;
+    u32 ninst;
+    u64* ctl;                  // 8 words per slot: [0] instance, [1..3] frontier counts
+    unsigned long long* stats; // instances, edges, levels, errors
+};
+
+__global__ void k_bfs_batch_fill(const __grid_constant__ gq_dev idq, const u32* order, u32 ninst, u64* err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (u32 i = 0; i < ninst; ++i)
+        if (queue_enqueue<unsigned int, GQ_LFQ>(idq, order[i], 0) != GQ_OK) atomicAdd(reinterpret_cast<unsigned long long*>(err), 1ull);
+}
+
+// Clears the cells an instance used and rewinds T and H (G-WFQ-YMC never reuses cells).
+__device__ void ymc_cluster_clear(const gq_dev& q, u32 ct, u32 nct, cg::cluster_group& cluster) {
+    // cells up to max(T, H), plus a margin for cells a slow-dequeue helper may
+    // have scanned past the completing candidate
+    const u64 used = max(ld_acq(q.ymc_tail), ld_acq(q.ymc_head)) + 65536;
+    const u64 hi = used < q.capacity ? used : q.capacity;
+    for (u64 i = 1 + ct; i <= hi; i += nct) {
+        q.cell_val[i] = ~0ull;
+        q.cell_enq[i] = 0;
+        q.cell_deq[i] = 0;
+    }
+    cluster.sync();
+    if (ct == 0) {
+        st_rel(q.ymc_tail, 1);
+        st_rel(q.ymc_head, 1);
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_bfs_batch(const __grid_constant__ gq_dev idq, const gq_dev* __restrict__ fq,
+                                                   const __grid_constant__ BatchK a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const u32 cblocks = cluster.num_blocks();
+    const u32 slot = blockIdx.x / cblocks;
+    const u32 ct = cluster.block_rank() * blockDim.x + threadIdx.x;    // thread id within the cluster
+    const u32 nct = cblocks * blockDim.x;
+    const u32 lane = threadIdx.x & 31;
+    const u32 cw = ct >> 5;
+    u64* ctl = a.ctl + 8 * (u64)slot;
+    const gq_dev& qa = fq[2 * slot];
+    const gq_dev& qb = fq[2 * slot + 1];
+    u64 edges = 0, levels_sum = 0, done = 0;
+    for (u32 guard = 0; guard < a.ninst + 1; ++guard) {
+        if (ct == 0) {
+            unsigned int id = 0;
+            const int s = queue_dequeue<unsigned int, GQ_LFQ>(idq, &id, slot);
+            st_rlx(ctl, s == GQ_OK ? id : kNoInstance);
+        }
+        cluster.sync();
+        const u32 id = (u32)ld_acq(ctl);
+        if (id == kNoInstance || id >= a.ninst) break;
+        const gq_bfs_instance g = a.inst[id];
+        for (u64 v = ct; v < g.n; v += nct) g.d_dist[v] = kUnreached;
+        if (ct == 0) {
+            st_rlx(ctl + 1, 0);
+            st_rlx(ctl + 2, 0);
+            st_rlx(ctl + 3, 0);
+        }
+        cluster.sync();
+        if (ct == 0) {
+            g.d_dist[g.src] = 0;
+            if (queue_enqueue<unsigned int, KIND>(qa, g.src, 0) == GQ_OK) st_rlx(ctl + 1, 1);
+        }
+        cluster.sync();
+        u32 level = 0;
+        for (;; ++level) {
+            const u64 frontier = ld_acq(ctl + 1 + level % 3);
+            if (frontier == 0) break;
+            if (ct == 0) st_rlx(ctl + 1 + (level + 2) % 3, 0);
+            const gq_dev& cur = (level & 1) ? qb : qa;
+            const gq_dev& nxt = (level & 1) ? qa : qb;
+            u32 cnt = 0;
+            if (cw < (frontier + 31) / 32 || cw < 1) {
+                bool active = true;
+                for (u32 round = 0; round < kRetryLimit; ++round) {
+                    unsigned int v = 0;
+                    int s = GQ_EMPTY;
+                    if (active) s = queue_dequeue<unsigned int, KIND>(cur, &v, ct);
+                    active = active && (s == GQ_OK);
+                    if (!__ballot_sync(0xffffffffu, active)) break;
+                    u64 b = 0, e = 0;
+                    if (active) {
+                        b = g.d_offsets[v];
+                        e = g.d_offsets[v + 1];
+                        if (e - b < 32) {
+                            edges += e - b;
+                            for (u64 k = b; k < e; ++k) bfs_visit<KIND>(nxt, g.d_dist, g.d_adj[k], level + 1, ct, &cnt);
+                        }
+                    }
+                    u32 big = __ballot_sync(0xffffffffu, active && (e - b >= 32));
+                    while (big) {
+                        const u32 owner = __ffs(big) - 1;
+                        big &= big - 1;
+                        const u64 bb = __shfl_sync(0xffffffffu, b, owner);
+                        const u64 ee = __shfl_sync(0xffffffffu, e, owner);
+                        if (lane == 0) edges += ee - bb;
+                        for (u64 k = bb + lane; k < ee; k += 32)
+                            bfs_visit<KIND>(nxt, g.d_dist, g.d_adj[k], level + 1, ct, &cnt);
+                        __syncwarp();
+                    }
+                }
+            }
+            warp_add_full(reinterpret_cast<unsigned long long*>(ctl + 1 + (level + 1) % 3), cnt);
+            cluster.sync();
+        }
+        if (KIND == GQ_YMC) {
+            ymc_cluster_clear(qa, ct, nct, cluster);
+            ymc_cluster_clear(qb, ct, nct, cluster);
+        }
+        if (ct == 0) {
+            levels_sum += level;
+            ++done;
+        }
+        cluster.sync();
+    }
+    if (a.stats) {
+        warp_add_full(a.stats + 1, edges);
+        if (ct == 0) {
+            atomicAdd(a.stats, done);
+            atomicAdd(a.stats + 2, levels_sum);
+        }
+    }
+}
+
+template <int KIND>
+int launch_bfs_batch(gq_handle idq, const gq_handle* fr, u32 slots, u32 cb, const gq_bfs_instance* inst,
+                     const u32* order, u32 ninst, void* ws, unsigned long long* stats, cudaStream_t st) {
+    char* b = static_cast<char*>(ws);
+    gq_dev* views = reinterpret_cast<gq_dev*>(b);
+    u64* ctl = reinterpret_cast<u64*>(b + (((u64)2 * slots * sizeof(gq_dev) + 255) / 256) * 256);
+    std::vector<gq_dev> h(2 * slots);
+    for (u32 i = 0; i < 2 * slots; ++i) h[i] = fr[i]->dev;
+    if (cudaMemcpyAsync(views, h.data(), h.size() * sizeof(gq_dev), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return GQ_ERR_CUDA;
+    if (cudaMemsetAsync(ctl, 0, (u64)slots * 64, st) != cudaSuccess) return GQ_ERR_CUDA;
+    k_bfs_batch_fill<<<1, 1, 0, st>>>(idq->dev, order, ninst, stats ? reinterpret_cast<u64*>(stats + 3) : ctl);
+    BatchK a{inst, order, ninst, ctl, stats};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(slots * cb);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cb;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    gq_dev iq = idq->dev;
+    const gq_dev* fv = views;
+    if (cudaLaunchKernelEx(&cfg, k_bfs_batch<KIND>, iq, fv, a) != cudaSuccess) return GQ_ERR_CUDA;
+    return gq_check_launch();
+}
+
 }  // namespace
+
+extern "C" int gq_bfs_batch_workspace_bytes(uint32_t slots, uint64_t* bytes) {
+    if (!slots || !bytes) return GQ_ERR_INVALID;
+    *bytes = (((uint64_t)2 * slots * sizeof(gq_dev) + 255) / 256) * 256 + (uint64_t)slots * 64;
+    return GQ_OK;
+}
+
+extern "C" int gq_bfs_batch(gq_handle id_queue, const gq_handle* frontier, uint32_t slots, uint32_t cluster_blocks,
+                            const gq_bfs_instance* d_instances, const uint32_t* d_order, uint32_t ninst,
+                            void* d_workspace, unsigned long long* d_stats, void* stream) {
+    if (!id_queue || !frontier || !slots || !d_instances || !d_order || !ninst || !d_workspace) return GQ_ERR_INVALID;
+    if (cluster_blocks != 1 && cluster_blocks != 2 && cluster_blocks != 4 && cluster_blocks != 8) return GQ_ERR_INVALID;
+    if (id_queue->dev.kind != GQ_LFQ || id_queue->dev.elem_bytes != 4 || id_queue->dev.capacity < ninst)
+        return GQ_ERR_INVALID;
+    const int kind = frontier[0]->dev.kind;
+    for (uint32_t i = 0; i < 2 * slots; ++i) {
+        if (!frontier[i] || frontier[i]->dev.kind != kind || frontier[i]->dev.elem_bytes != 4 ||
+            frontier[i]->device != id_queue->device)
+            return GQ_ERR_INVALID;
+        if (kind != GQ_LFQ && frontier[i]->dev.max_threads < cluster_blocks * 256) return GQ_ERR_TOO_MANY_THREADS;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (d_stats && cudaMemsetAsync(d_stats, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess) return GQ_ERR_CUDA;
+    switch (kind) {
+        case GQ_LFQ: return launch_bfs_batch<GQ_LFQ>(id_queue, frontier, slots, cluster_blocks, d_instances, d_order, ninst, d_workspace, d_stats, st);
+        case GQ_WFQ: return launch_bfs_batch<GQ_WFQ>(id_queue, frontier, slots, cluster_blocks, d_instances, d_order, ninst, d_workspace, d_stats, st);
+        default: return launch_bfs_batch<GQ_YMC>(id_queue, frontier, slots, cluster_blocks, d_instances, d_order, ninst, d_workspace, d_stats, st);
+    }
+}
 
 extern "C" int gq_bfs(gq_handle q_a, gq_handle q_b, uint64_t n, const uint64_t* d_offsets, const uint32_t* d_adj,
                       uint32_t src, uint32_t* d_dist, unsigned long long* d_stats, void* stream) {
