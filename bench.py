@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-threads", type=int, default=1 << 17, help="logical threads in the CPU sample")
-    p.add_argument("--no-apps", action="store_true", help="skip the application measurements (BFS)")
+    p.add_argument("--no-apps", action="store_true", help="skip the application measurements (BFS, ray tracing)")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched / persistent / graph comparisons")
     return p.parse_args()
 
 
@@ -192,6 +193,105 @@ def bench_apps(gq, synth, kinds, dev, reps=3):
                                       "alu_frac_of_peak": round(flops / (t * 1e-3) / peak, 3)}
         for q in r.queues:
             q.close()
+    return out
+
+
+def _timed(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms))
+
+
+def bench_batched(gq, synth, kinds, dev, reps=3):
+    """Batched forms against the plain per-call form on the same GPU.
+    (1) 256 independent queues, capacities log-uniform 2^8 .. 2^16 (seed 0),
+        2^18 threads (1024 per queue), 10^7 operations, 50 % producers; one step
+        resets every queue and runs the workload: per-call = 256 launches,
+        persistent = one launch, graph = the step captured and replayed,
+        tuned = autotuned batch width / blocks / back-off, graph-replayed.
+    (2) 64 BFS instances, R-MAT scale uniform in 12 .. 18 (seed 11): per-call =
+        one gq_bfs per instance, batched = one persistent launch (8-block clusters)."""
+    import torch
+    from paper_2606_01693_gb300 import autotune
+    out = {}
+    Q, TPQ, OPS = 256, 1024, 10 ** 7
+    OPQ, PPQ = OPS // Q, TPQ // 2
+    r = synth.splitmix64(0, np.arange(Q)) >> np.uint64(40)
+    caps = 1 << (8 + (r.astype(np.float64) * 2.0**-24 * 9).astype(np.int64))
+    for k in kinds:
+        qc = caps if k != "ymc" else np.full(Q, 3 * OPQ + (1 << 12))
+        mq = gq.MultiQueue(k, qc, 8, TPQ)
+        counts = torch.zeros(8, dtype=torch.int64, device=dev)
+
+        def succ():
+            c = counts.cpu().numpy()
+            return float(c[0] + c[2])
+
+        def per_call():
+            counts.zero_()
+            for q in mq.queues:
+                q.reset()
+            mq.run_per_call(TPQ, PPQ, OPQ, counts)
+
+        def persistent():
+            counts.zero_()
+            mq.reset()
+            mq.run(TPQ, PPQ, OPQ, counts)
+
+        res = {}
+        t = _timed(per_call, reps)
+        res["per_call_mops"] = round(succ() / (t * 1e-3) / 1e6, 1)
+        t = _timed(persistent, reps)
+        res["persistent_mops"] = round(succ() / (t * 1e-3) / 1e6, 1)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            persistent()
+        t = _timed(g.replay, reps)
+        res["graph_mops"] = round(succ() / (t * 1e-3) / 1e6, 1)
+        best = autotune.tune_multi(mq, TPQ, PPQ, OPQ, reps=2)
+        g2 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g2):
+            counts.zero_()
+            mq.reset()
+            mq.run(TPQ, PPQ, OPQ, counts, blocks=best["blocks"])
+        t = _timed(g2.replay, reps)
+        res["tuned_graph_mops"] = round(succ() / (t * 1e-3) / 1e6, 1)
+        res["tuned"] = {kk: best[kk] for kk in ("batch_width", "blocks", "backoff_ns")}
+        out["queues256_%s" % k] = res
+        mq.close()
+    # batched BFS
+    rr = synth.splitmix64(11, np.arange(64)) >> np.uint64(40)
+    scales = 12 + (rr.astype(np.float64) * 2.0**-24 * 7).astype(np.int64)
+    graphs = [synth.rmat_csr_fast(int(sc), seed=11000 + i) for i, sc in enumerate(scales)]
+    sources = [0] * len(graphs)
+    for k in kinds:
+        b = gq.BatchBfs(k, graphs, sources, slots=64, cluster_blocks=8)
+        t_b = _timed(b.run, reps)
+        nmax = max(len(o) - 1 for o, _ in graphs)
+        cap = 3 * nmax + 64 * 65 + (1 << 16) if k == "ymc" else min(1 << max(12, (nmax - 1).bit_length()), 1 << 23)
+        qa, qb = gq.Queue(k, cap, 4, 1 << 19), gq.Queue(k, cap, 4, 1 << 19)
+        st = torch.zeros(4, dtype=torch.int64, device=dev)
+
+        def per_call_bfs():
+            for (d_off, d_adj, dist) in b.graphs:
+                qa.reset()
+                qb.reset()
+                gq.gq_bfs(qa.handle, qb.handle, d_off, d_adj, 0, dist, st)
+
+        t_p = _timed(per_call_bfs, reps)
+        out["bfs64_%s" % k] = {"per_call_ms": round(t_p, 2), "batched_ms": round(t_b, 2),
+                               "speedup": round(t_p / t_b, 2)}
+        qa.close()
+        qb.close()
     return out
 
 
@@ -437,6 +537,9 @@ def main():
     apps = None
     if not args.no_apps:
         apps = bench_apps(gq, synth, kinds, dev)
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(gq, synth, kinds, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -454,7 +557,7 @@ def main():
                            "l2": "flushed between timed steps (256 MiB write); queue state re-initialised inside "
                                  "each step"},
                 "roofline": roofline, "peaks": peaks, "per_queue": per_queue, "sweep": sweep,
-                "cpu_baseline": cpu, "e2e": e2e, "apps": apps,
+                "cpu_baseline": cpu, "e2e": e2e, "apps": apps, "batched": batched,
                 "gpu_launches": args.steps * sum(launches_per_step[k] for k in kinds),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
