@@ -106,9 +106,9 @@ int gq_atomic_peak(int pattern, uint32_t blocks, uint32_t threads, uint32_t iter
  *
  * gq_multi_prepare copies the device views of Q queues (same kind and element
  * size) into d_views (Q * sizeof(gq_dev) bytes of device memory; sizeof(gq_dev)
- * never exceeds GQ_VIEW_BYTES).  `tune`
- * (nullable) overrides the WaveFAA batch width and the back-off of every copied
- * view (0 fields keep the queue's own), which is how the autotuner tries
+ * never exceeds GQ_VIEW_BYTES).  `tune` (nullable) overrides, in every copied
+ * view, the WaveFAA batch width (if non-zero), the back-off, and, when
+ * tune->patience_set is 1, G-WFQ's patience; this is how the autotuner tries
  * settings without recreating queues.  Asynchronous on `stream`. */
 int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void* d_views, const gq_options* tune,
                      void* stream);

@@ -39,9 +39,13 @@ def _save_cache(c: dict) -> None:
 
 def tune_multi(mq, threads_per_queue: int, producers_per_queue: int, ops_per_queue: int,
                widths=(32, 16, 8, 4, 1), blocks_per_sm=(0, 2, 4, 8), backoffs=(0, 100, 400), reps: int = 3,
-               use_cache: bool = True, block: int = 256) -> dict:
-    """Returns {"batch_width", "blocks", "backoff_ns", "mops", "table"} for MultiQueue `mq`
-    and leaves `mq` prepared with the winning settings."""
+               use_cache: bool = True, block: int = 256, patiences=None) -> dict:
+    """Returns {"batch_width", "blocks", "backoff_ns", "patience", "mops", "table"} for
+    MultiQueue `mq` and leaves `mq` prepared with the winning settings.  G-WFQ
+    queues also try the patience pairs (enqueue, dequeue) in `patiences`
+    (default (16, 64), (64, 256), (256, 1024))."""
+    if patiences is None:
+        patiences = [(16, 64), (64, 256), (256, 1024)] if mq.kind == 1 else [None]
     import torch
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     key = "%s|kind%d|q%d|tpq%d|ppq%d|opq%d|cap%d" % (props.name, mq.kind, len(mq.queues), threads_per_queue,
@@ -50,31 +54,33 @@ def tune_multi(mq, threads_per_queue: int, producers_per_queue: int, ops_per_que
     cache = _load_cache() if use_cache else {}
     if use_cache and key in cache:
         best = cache[key]
-        mq.prepare(batch_width=best["batch_width"], backoff_ns=best["backoff_ns"])
+        pat = tuple(best["patience"]) if best.get("patience") else None
+        mq.prepare(batch_width=best["batch_width"], backoff_ns=best["backoff_ns"], patience=pat)
         return dict(best, cached=True)
     counts = torch.zeros(8, dtype=torch.int64, device="cuda")
     table = []
-    for w in widths:
-        for bo in backoffs:
-            mq.prepare(batch_width=w, backoff_ns=bo)
-            for bps in blocks_per_sm:
-                blocks = bps * props.multi_processor_count
-                ms = []
-                for r in range(reps + 1):
-                    mq.reset()
-                    counts.zero_()
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record()
-                    mq.run(threads_per_queue, producers_per_queue, ops_per_queue, counts, block=block, blocks=blocks)
-                    e1.record()
-                    e1.synchronize()
-                    if r:
-                        ms.append(e0.elapsed_time(e1))
-                c = counts.cpu().numpy()
-                mops = float(c[0] + c[2]) / (float(np.median(ms)) * 1e-3) / 1e6
-                table.append({"batch_width": w, "backoff_ns": bo, "blocks": blocks, "mops": round(mops, 1)})
+    for w, bo, pat in [(w, bo, pat) for w in widths for bo in backoffs for pat in patiences]:
+        mq.prepare(batch_width=w, backoff_ns=bo, patience=pat)
+        for bps in blocks_per_sm:
+            blocks = bps * props.multi_processor_count
+            ms = []
+            for r in range(reps + 1):
+                mq.reset()
+                counts.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                mq.run(threads_per_queue, producers_per_queue, ops_per_queue, counts, block=block, blocks=blocks)
+                e1.record()
+                e1.synchronize()
+                if r:
+                    ms.append(e0.elapsed_time(e1))
+            c = counts.cpu().numpy()
+            mops = float(c[0] + c[2]) / (float(np.median(ms)) * 1e-3) / 1e6
+            table.append({"batch_width": w, "backoff_ns": bo, "blocks": blocks, "patience": pat,
+                          "mops": round(mops, 1)})
     best = max(table, key=lambda r: r["mops"])
-    mq.prepare(batch_width=best["batch_width"], backoff_ns=best["backoff_ns"])
+    pat = tuple(best["patience"]) if best.get("patience") else None
+    mq.prepare(batch_width=best["batch_width"], backoff_ns=best["backoff_ns"], patience=pat)
     out = dict(best)
     if use_cache:
         cache[key] = out

@@ -220,11 +220,15 @@ int launch_multi(const gq_dev* views, const gq_multi_args& g, cudaStream_t st) {
     return gq_check_launch();
 }
 
-__global__ void k_multi_tune(gq_dev* views, u32 n, u32 width, u32 backoff, u32 set_backoff) {
+__global__ void k_multi_tune(gq_dev* views, u32 n, u32 width, u32 backoff, u32 set_patience, u32 pe, u32 pd) {
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (width) views[i].batch_width = width;
-    if (set_backoff) views[i].backoff_ns = backoff;
+    views[i].backoff_ns = backoff;
+    if (set_patience && views[i].kind == GQ_WFQ) {
+        views[i].patience_enq = pe;
+        views[i].patience_deq = pd;
+    }
 }
 
 }  // namespace
@@ -244,7 +248,8 @@ extern "C" int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void*
         if (cudaMemcpyAsync(v + i, &queues[i]->dev, sizeof(gq_dev), cudaMemcpyHostToDevice, st) != cudaSuccess)
             return GQ_ERR_CUDA;
     if (tune) {
-        k_multi_tune<<<(nqueues + 255) / 256, 256, 0, st>>>(v, nqueues, tune->batch_width, tune->backoff_ns, 1);
+        k_multi_tune<<<(nqueues + 255) / 256, 256, 0, st>>>(v, nqueues, tune->batch_width, tune->backoff_ns,
+                                                            tune->patience_set, tune->patience_enq, tune->patience_deq);
         return gq_check_launch();
     }
     return GQ_OK;
