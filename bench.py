@@ -257,7 +257,8 @@ def bench_batched(gq, synth, kinds, dev, reps=3):
             persistent()
         t = _timed(g.replay, reps)
         res["graph_mops"] = round(succ() / (t * 1e-3) / 1e6, 1)
-        best = autotune.tune_multi(mq, TPQ, PPQ, OPQ, reps=2)
+        best = autotune.tune_multi(mq, TPQ, PPQ, OPQ, widths=(32, 16, 8), blocks_per_sm=(0, 4), backoffs=(0, 200),
+                                   reps=2)
         g2 = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g2):
             counts.zero_()

@@ -1,0 +1,87 @@
+/*
+ * gq_serve.h -- C ABI of the BFS serving runtime built on the queues.
+ *
+ * Requests (graph id, source vertex) arrive at given times; each asks for the
+ * hop distances of a level-synchronous BFS (Section V-B) on one graph of a
+ * resident pool.  Two ways to serve them on one GPU:
+ *   GQ_SERVE_PERSISTENT   one persistent device scheduler: thread-block
+ *                         clusters claim request tickets from a device counter,
+ *                         wait (bounded polling) until the host has published
+ *                         the ticket in a request ring in mapped pinned memory
+ *                         (system-scope release / acquire), run the BFS on the
+ *                         cluster's own pair of frontier queues, and mark the
+ *                         ring entry done (system-scope release), which the host
+ *                         polls.  Requests that arrive while others run are
+ *                         taken as soon as a cluster frees up.
+ *   GQ_SERVE_PER_REQUEST  the plain form: one gq_bfs launch per request
+ *                         (the whole GPU, one request at a time), in arrival
+ *                         order on one stream; completion is an event the host
+ *                         polls.
+ * Admission (both modes, first come first served): a request is published or
+ * launched only when its device state fits in the budget; it waits on the host
+ * otherwise.  A request's state is counted as its graph's CSR (8 (n + 1) +
+ * 4 m bytes), its distance array (4 n bytes) and two frontier queues of its own
+ * size (gq_workspace_bytes of the kind at capacity max(n, 4096) rounded up to
+ * a power of two; G-WFQ-YMC: 4 n + 2^18 cells).
+ * Latency = the time the host sees the request done minus its arrival time.
+ * A request's distances do not depend on what else is being served: BFS hop
+ * counts are unique, whatever the claim order.
+ */
+#ifndef GQ_SERVE_H
+#define GQ_SERVE_H
+
+#include <stdint.h>
+
+#include "gq_apps.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { GQ_SERVE_PERSISTENT = 0, GQ_SERVE_PER_REQUEST = 1 };
+
+typedef struct {
+    int32_t kind;                   /* frontier queue kind (gq_kind)                           */
+    uint32_t mode;                  /* GQ_SERVE_*                                              */
+    uint32_t slots;                 /* persistent: clusters serving at once; 0 = all that fit  */
+                                    /* on the GPU at once (fewer are used if fewer fit)       */
+    uint32_t cluster_blocks;        /* persistent: blocks of 256 threads per cluster: 1,2,4,8  */
+    uint64_t budget_bytes;          /* admission budget for per-request state                  */
+    double wait_limit_s;            /* bound on any one wait of the device scheduler for its   */
+                                    /* next request, and on the host's wait for progress;     */
+                                    /* 0 = 30 s                                                */
+    uint32_t ngraphs;
+    uint32_t nrequests;
+    const gq_bfs_instance* graphs;  /* host array [ngraphs]; n, d_offsets, d_adj are used      */
+    const uint32_t* req_graph;      /* host arrays [nrequests]                                 */
+    const uint32_t* req_src;
+    const double* req_arrival_s;    /* arrival offsets from the start, seconds, non-decreasing */
+    uint32_t* const* req_out;       /* nullable host array [nrequests] of device pointers; a  */
+                                    /* non-null entry receives that request's distances (n    */
+                                    /* uint32, GQ_BFS_UNREACHED where unreached); null entries */
+                                    /* (or a null array) use scratch from a device arena of at */
+                                    /* most budget_bytes                                      */
+} gq_serve_config;
+
+typedef struct {
+    double* latency_s;              /* caller array [nrequests], filled                        */
+    double wall_s;                  /* first arrival to last completion                        */
+    uint64_t peak_state_bytes;      /* largest admitted state counted at one time              */
+    uint64_t admission_waits;       /* requests that had arrived but waited for budget         */
+    uint64_t edges_scanned;         /* persistent mode: edges scanned over all requests        */
+    uint32_t slots_used;            /* persistent mode: clusters launched                      */
+    int32_t status;                 /* GQ_OK or the first error                                */
+} gq_serve_result;
+
+/* Serves every request and returns when all are done (synchronous; uses the
+ * current device; creates and frees its own queues, arena, ring and stream).
+ * res->latency_s must hold nrequests doubles.
+ * Errors: GQ_ERR_INVALID (bad configuration, a graph id or source out of
+ * range, a request whose state exceeds the budget), GQ_ERR_NOMEM, GQ_ERR_CUDA,
+ * GQ_ERR_TIMEOUT (a bounded wait expired), or an error latched by a queue. */
+int gq_serve(const gq_serve_config* cfg, gq_serve_result* res);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GQ_SERVE_H */

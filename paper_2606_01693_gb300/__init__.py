@@ -1,7 +1,8 @@
 """Python binding of libgq: linearizable concurrent FIFO queues on one GB300.
 
 Thin argument marshalling over the C ABI in ``include/gq.h`` and
-``include/gq_drivers.h`` (same function names).  Every queue operation runs in
+``include/gq_drivers.h``, ``include/gq_apps.h`` and ``include/gq_serve.h``
+(same function names).  Every queue operation runs in
 the CUDA kernels of ``libgq.so``; PyTorch only supplies device memory and the
 current stream.  There is no CPU fallback: if the library cannot be loaded,
 every call raises.
@@ -36,7 +37,7 @@ EXPORTS = [
     "gq_sync_status", "gq_device_view", "gq_info", "gq_status_str", "gq_get_stats",
     "gq_run", "gq_run_sequence", "gq_drain", "gq_atomic_peak", "gq_fifo_static_roundtrip",
     "gq_bfs", "gq_render_workspace_bytes", "gq_render", "gq_multi_prepare", "gq_run_multi",
-    "gq_bfs_batch_workspace_bytes", "gq_bfs_batch",
+    "gq_bfs_batch_workspace_bytes", "gq_bfs_batch", "gq_serve",
 ]
 GQ_VIEW_BYTES = 512
 
@@ -102,6 +103,7 @@ def load() -> ctypes.CDLL:
         "gq_run_multi": [P, P, P],
         "gq_bfs_batch_workspace_bytes": [u32, P],
         "gq_bfs_batch": [P, P, u32, u32, P, P, u32, P, P, P],
+        "gq_serve": [P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -453,3 +455,58 @@ class Queue:
             self.close()
         except Exception:
             pass
+
+
+# ---- serving (include/gq_serve.h) ----
+GQ_SERVE_PERSISTENT, GQ_SERVE_PER_REQUEST = 0, 1
+SERVE_MODES = {"persistent": GQ_SERVE_PERSISTENT, "per_request": GQ_SERVE_PER_REQUEST}
+
+
+class gq_serve_config(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("mode", ctypes.c_uint32), ("slots", ctypes.c_uint32),
+                ("cluster_blocks", ctypes.c_uint32), ("budget_bytes", ctypes.c_uint64),
+                ("wait_limit_s", ctypes.c_double), ("ngraphs", ctypes.c_uint32), ("nrequests", ctypes.c_uint32),
+                ("graphs", ctypes.c_void_p), ("req_graph", ctypes.c_void_p), ("req_src", ctypes.c_void_p),
+                ("req_arrival_s", ctypes.c_void_p), ("req_out", ctypes.c_void_p)]
+
+
+class gq_serve_result(ctypes.Structure):
+    _fields_ = [("latency_s", ctypes.c_void_p), ("wall_s", ctypes.c_double), ("peak_state_bytes", ctypes.c_uint64),
+                ("admission_waits", ctypes.c_uint64), ("edges_scanned", ctypes.c_uint64),
+                ("slots_used", ctypes.c_uint32), ("status", ctypes.c_int32)]
+
+
+def gq_serve(kind, graphs, req_graph, req_src, arrival_s, mode="persistent", slots: int = 0,
+             cluster_blocks: int = 4, budget_bytes: int = 32 << 30, outs=None, wait_limit_s: float = 0.0) -> dict:
+    """Serves BFS requests (include/gq_serve.h).
+
+    graphs: list of (d_offsets int64, d_adj int32) device tensors (CSR).
+    req_graph, req_src: request graph ids and source vertices; arrival_s:
+    non-decreasing arrival offsets in seconds.  outs: optional list of device
+    int32 tensors (or None entries) receiving each request's distances.
+    Returns latencies (numpy, seconds) and the run's counters."""
+    import numpy as np
+    lib = load()
+    kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+    mode = SERVE_MODES[mode] if isinstance(mode, str) else int(mode)
+    g = (gq_bfs_instance * len(graphs))()
+    for i, (off, adj) in enumerate(graphs):
+        g[i] = gq_bfs_instance(off.numel() - 1, off.data_ptr(), adj.data_ptr(), None, 0, 0)
+    rg = np.ascontiguousarray(req_graph, dtype=np.uint32)
+    rs = np.ascontiguousarray(req_src, dtype=np.uint32)
+    ra = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    n = len(rg)
+    if len(rs) != n or len(ra) != n:
+        raise ValueError("request arrays differ in length")
+    out_arr = None
+    if outs is not None:
+        out_arr = (ctypes.c_void_p * n)(*[None if o is None else o.data_ptr() for o in outs])
+    lat = np.full(n, -1.0)
+    cfg = gq_serve_config(kind, mode, slots, cluster_blocks, budget_bytes, wait_limit_s, len(graphs), n,
+                          ctypes.cast(g, ctypes.c_void_p), rg.ctypes.data, rs.ctypes.data, ra.ctypes.data,
+                          None if out_arr is None else ctypes.cast(out_arr, ctypes.c_void_p))
+    res = gq_serve_result(lat.ctypes.data, 0.0, 0, 0, 0, 0, 0)
+    _check(lib.gq_serve(ctypes.byref(cfg), ctypes.byref(res)), "gq_serve")
+    return {"latency_s": lat, "wall_s": res.wall_s, "peak_state_bytes": res.peak_state_bytes,
+            "admission_waits": res.admission_waits, "edges_scanned": res.edges_scanned,
+            "slots_used": res.slots_used}

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgq.so")
-SOURCES = ["gq_api.cu", "gq_drivers.cu", "gq_peaks.cu", "gq_static.cu", "gq_apps.cu", "gq_rt.cu"]
+SOURCES = ["gq_api.cu", "gq_drivers.cu", "gq_peaks.cu", "gq_static.cu", "gq_apps.cu", "gq_rt.cu", "gq_serve.cu"]
 # per-file flags: the ray tracer's radiance must round like the sequential CPU trace
 EXTRA = {"gq_rt.cu": ["-fmad=false", "-prec-div=true", "-prec-sqrt=true", "-ftz=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

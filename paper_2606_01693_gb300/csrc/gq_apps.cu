@@ -16,14 +16,13 @@
 #include <vector>
 
 #include "../../include/gq_apps.h"
+#include "gq_bfs.cuh"
 #include "gq_host.h"
-#include "gq_ops.cuh"
 
 using namespace gqd;
 
 namespace {
 
-constexpr u32 kUnreached = 0xFFFFFFFFu;
 constexpr u32 kBarrierSpinLimit = 1u << 26;   // x ~100 ns sleeps: a few seconds
 
 // Control words in the first queue's scratch line (words 8..15).
@@ -58,13 +57,6 @@ __device__ __forceinline__ bool grid_barrier(u64* ctl, u32 nblocks) {
     }
     __syncthreads();
     return s_ok != 0;
-}
-
-template <int KIND>
-__device__ __forceinline__ void bfs_visit(const gq_dev& nxt, u32* dist, u32 w, u32 next_level, u32 tid, u32* cnt) {
-    if (aref<u32>(dist[w]).load(kRlx) != kUnreached) return;
-    if (atomicCAS(dist + w, kUnreached, next_level) != kUnreached) return;
-    if (queue_enqueue<unsigned int, KIND>(nxt, w, tid) == GQ_OK) ++*cnt;
 }
 
 template <int KIND>
@@ -159,7 +151,6 @@ int launch_bfs(gq_handle ha, gq_handle hb, uint64_t n, const uint64_t* off, cons
 // ---------------------------------------------------------------------------
 // Batched BFS: one instance per thread-block cluster at a time
 // ---------------------------------------------------------------------------
-namespace cg = cooperative_groups;
 
 constexpr u32 kNoInstance = 0xFFFFFFFFu;
 
@@ -177,24 +168,6 @@ __global__ void k_bfs_batch_fill(const __grid_constant__ gq_dev idq, const u32* 
         if (queue_enqueue<unsigned int, GQ_LFQ>(idq, order[i], 0) != GQ_OK) atomicAdd(reinterpret_cast<unsigned long long*>(err), 1ull);
 }
 
-// Clears the cells an instance used and rewinds T and H (G-WFQ-YMC never reuses cells).
-__device__ void ymc_cluster_clear(const gq_dev& q, u32 ct, u32 nct, cg::cluster_group& cluster) {
-    // cells up to max(T, H), plus a margin for cells a slow-dequeue helper may
-    // have scanned past the completing candidate
-    const u64 used = max(ld_acq(q.ymc_tail), ld_acq(q.ymc_head)) + 65536;
-    const u64 hi = used < q.capacity ? used : q.capacity;
-    for (u64 i = 1 + ct; i <= hi; i += nct) {
-        q.cell_val[i] = ~0ull;
-        q.cell_enq[i] = 0;
-        q.cell_deq[i] = 0;
-    }
-    cluster.sync();
-    if (ct == 0) {
-        st_rel(q.ymc_tail, 1);
-        st_rel(q.ymc_head, 1);
-    }
-}
-
 template <int KIND>
 __global__ void __launch_bounds__(256) k_bfs_batch(const __grid_constant__ gq_dev idq, const gq_dev* __restrict__ fq,
                                                    const __grid_constant__ BatchK a) {
@@ -203,8 +176,6 @@ __global__ void __launch_bounds__(256) k_bfs_batch(const __grid_constant__ gq_de
     const u32 slot = blockIdx.x / cblocks;
     const u32 ct = cluster.block_rank() * blockDim.x + threadIdx.x;    // thread id within the cluster
     const u32 nct = cblocks * blockDim.x;
-    const u32 lane = threadIdx.x & 31;
-    const u32 cw = ct >> 5;
     u64* ctl = a.ctl + 8 * (u64)slot;
     const gq_dev& qa = fq[2 * slot];
     const gq_dev& qb = fq[2 * slot + 1];
@@ -217,70 +188,14 @@ __global__ void __launch_bounds__(256) k_bfs_batch(const __grid_constant__ gq_de
         }
         cluster.sync();
         const u32 id = (u32)ld_acq(ctl);
+        cluster.sync();                      // everyone has read the id before ctl is reused
         if (id == kNoInstance || id >= a.ninst) break;
         const gq_bfs_instance g = a.inst[id];
-        for (u64 v = ct; v < g.n; v += nct) g.d_dist[v] = kUnreached;
+        const u32 lv = cluster_bfs<KIND>(qa, qb, ctl + 1, g, g.d_dist, ct, nct, cluster, &edges);
         if (ct == 0) {
-            st_rlx(ctl + 1, 0);
-            st_rlx(ctl + 2, 0);
-            st_rlx(ctl + 3, 0);
-        }
-        cluster.sync();
-        if (ct == 0) {
-            g.d_dist[g.src] = 0;
-            if (queue_enqueue<unsigned int, KIND>(qa, g.src, 0) == GQ_OK) st_rlx(ctl + 1, 1);
-        }
-        cluster.sync();
-        u32 level = 0;
-        for (;; ++level) {
-            const u64 frontier = ld_acq(ctl + 1 + level % 3);
-            if (frontier == 0) break;
-            if (ct == 0) st_rlx(ctl + 1 + (level + 2) % 3, 0);
-            const gq_dev& cur = (level & 1) ? qb : qa;
-            const gq_dev& nxt = (level & 1) ? qa : qb;
-            u32 cnt = 0;
-            if (cw < (frontier + 31) / 32 || cw < 1) {
-                bool active = true;
-                for (u32 round = 0; round < kRetryLimit; ++round) {
-                    unsigned int v = 0;
-                    int s = GQ_EMPTY;
-                    if (active) s = queue_dequeue<unsigned int, KIND>(cur, &v, ct);
-                    active = active && (s == GQ_OK);
-                    if (!__ballot_sync(0xffffffffu, active)) break;
-                    u64 b = 0, e = 0;
-                    if (active) {
-                        b = g.d_offsets[v];
-                        e = g.d_offsets[v + 1];
-                        if (e - b < 32) {
-                            edges += e - b;
-                            for (u64 k = b; k < e; ++k) bfs_visit<KIND>(nxt, g.d_dist, g.d_adj[k], level + 1, ct, &cnt);
-                        }
-                    }
-                    u32 big = __ballot_sync(0xffffffffu, active && (e - b >= 32));
-                    while (big) {
-                        const u32 owner = __ffs(big) - 1;
-                        big &= big - 1;
-                        const u64 bb = __shfl_sync(0xffffffffu, b, owner);
-                        const u64 ee = __shfl_sync(0xffffffffu, e, owner);
-                        if (lane == 0) edges += ee - bb;
-                        for (u64 k = bb + lane; k < ee; k += 32)
-                            bfs_visit<KIND>(nxt, g.d_dist, g.d_adj[k], level + 1, ct, &cnt);
-                        __syncwarp();
-                    }
-                }
-            }
-            warp_add_full(reinterpret_cast<unsigned long long*>(ctl + 1 + (level + 1) % 3), cnt);
-            cluster.sync();
-        }
-        if (KIND == GQ_YMC) {
-            ymc_cluster_clear(qa, ct, nct, cluster);
-            ymc_cluster_clear(qb, ct, nct, cluster);
-        }
-        if (ct == 0) {
-            levels_sum += level;
+            levels_sum += lv;
             ++done;
         }
-        cluster.sync();
     }
     if (a.stats) {
         warp_add_full(a.stats + 1, edges);

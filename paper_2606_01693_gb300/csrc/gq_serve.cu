@@ -1,0 +1,571 @@
+// BFS serving runtime (include/gq_serve.h): a persistent device scheduler fed
+// by a host request ring in mapped pinned memory, and the per-request-launch
+// form it is measured against.
+//
+// Device side.  One persistent launch of `slots` thread-block clusters.  Each
+// cluster's thread 0 takes the next request ticket with a fetch-add on a
+// device counter and polls the ring entry of that ticket (system-scope
+// acquire) until the host has published it, sleeping between polls; the wait
+// is bounded by %globaltimer and a host stop word.  It hands the request to the
+// cluster through device-memory control words, the cluster runs the
+// level-synchronous BFS on its own two frontier queues (hardware cluster
+// barrier between levels), and thread 0 marks the entry done with a
+// system-scope release after a system fence.  Tickets >= the request count end
+// the cluster.
+//
+// Host side (native, in this file).  One thread runs arrivals, admission and
+// completion: it publishes each request once its arrival time has passed, its
+// ring entry is free (the request one ring-length earlier is done) and its
+// state fits in the budget (first come first served); scratch distance arrays
+// come from a first-fit arena with coalescing.  It polls the done words of the
+// requests in flight and records latencies.  If the scheduler kernel ends
+// before every request is done, or nothing progresses for the wait limit, it
+// raises the stop word and reports the error.
+#include <cuda/atomic>
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstring>
+#include <iterator>
+#include <map>
+#include <vector>
+
+#include "../../include/gq_serve.h"
+#include "gq_bfs.cuh"
+#include "gq_host.h"
+
+using namespace gqd;
+
+namespace {
+
+// One 64-byte ring entry in mapped pinned memory.
+struct ServeEntry {
+    u64 seq;      // host: ticket + 1 once the fields below are valid (release)
+    u64 done;     // device: ticket + 1 once the distances are written (release, system scope)
+    u64 req;      // host: graph id | source << 32
+    u64 dist;     // host: device address of the request's distance array
+    u64 levels;   // device: levels of the search
+    u64 pad[3];
+};
+static_assert(sizeof(ServeEntry) == 64, "ring entries are one 64-byte line");
+
+// Words the host writes in mapped pinned memory (the device only loads them:
+// no atomic read-modify-write touches host memory).
+struct ServeShared {
+    u64 stop;     // 1 = every cluster leaves at its next wait
+    u64 pad[15];
+};
+
+constexpr u64 kNoTicket = ~0ull;
+
+struct ServeK {
+    ServeEntry* ring;            // device view of the mapped ring
+    ServeShared* sh;             // device view of the mapped shared words
+    const gq_bfs_instance* graphs;
+    u32 ngraphs, ring_mask;
+    u64 nreq;
+    u64* claim;                  // next ticket (device memory)
+    u64* ctl;                    // 8 words per slot (device memory)
+    unsigned long long* stats;   // edges scanned, requests served, first error (1 = wait limit, 2 = bad request)
+    u64 wait_ns;
+};
+
+using sys_ref = cuda::atomic_ref<u64, cuda::thread_scope_system>;
+
+__device__ __forceinline__ u64 ld_acq_sys(u64* p) { return sys_ref(*p).load(kAcq); }
+__device__ __forceinline__ u64 ld_rlx_sys(u64* p) { return sys_ref(*p).load(kRlx); }
+__device__ __forceinline__ void st_rel_sys(u64* p, u64 v) { sys_ref(*p).store(v, kRel); }
+__device__ __forceinline__ void st_rlx_sys(u64* p, u64 v) { sys_ref(*p).store(v, kRlx); }
+
+// Thread 0 of a cluster: the next ticket whose entry the host has published,
+// with its fields copied into ctl[4..5]; kNoTicket when there is none left,
+// the host asked to stop, or the wait limit expired (error latched).
+__device__ u64 claim_request(const ServeK& a, u64* ctl) {
+    const u64 t = faa_rlx(a.claim, 1);
+    if (t >= a.nreq) return kNoTicket;
+    ServeEntry* e = a.ring + (t & a.ring_mask);
+    const u64 t0 = globaltimer();
+    for (u32 polls = 0;; ++polls) {
+        if (ld_acq_sys(&e->seq) == t + 1) break;
+        if (ld_rlx_sys(&a.sh->stop)) return kNoTicket;
+        if (globaltimer() - t0 > a.wait_ns) {
+            atomicCAS(a.stats + 2, 0ull, 1ull);
+            return kNoTicket;
+        }
+        __nanosleep(polls < 256 ? 64 : 256);
+    }
+    const u64 req = ld_rlx_sys(&e->req);
+    const u32 g = (u32)req, s = (u32)(req >> 32);
+    if (g >= a.ngraphs || s >= a.graphs[g].n) {
+        atomicCAS(a.stats + 2, 0ull, 2ull);
+        st_rlx_sys(&e->levels, ~0ull);
+        st_rel_sys(&e->done, t + 1);
+        return kNoTicket;
+    }
+    st_rlx(ctl + 4, ((u64)s << 32) | g);
+    st_rlx(ctl + 5, ld_rlx_sys(&e->dist));
+    return t;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_serve(const gq_dev* __restrict__ fq, const __grid_constant__ ServeK a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const u32 cblocks = cluster.num_blocks();
+    const u32 slot = blockIdx.x / cblocks;
+    const u32 ct = cluster.block_rank() * blockDim.x + threadIdx.x;
+    const u32 nct = cblocks * blockDim.x;
+    u64* ctl = a.ctl + 8 * (u64)slot;     // [0] ticket, [1..3] frontier counts, [4] src|graph, [5] dist
+    const gq_dev& qa = fq[2 * slot];
+    const gq_dev& qb = fq[2 * slot + 1];
+    u64 edges = 0, served = 0;
+    for (u64 guard = 0; guard <= a.nreq; ++guard) {
+        if (ct == 0) st_rlx(ctl, claim_request(a, ctl));
+        cluster.sync();
+        const u64 t = ld_acq(ctl);
+        const u64 gs = ld_acq(ctl + 4);
+        u32* dist = reinterpret_cast<u32*>(ld_acq(ctl + 5));
+        cluster.sync();                      // every thread has read ctl before it is reused
+        if (t == kNoTicket) break;
+        gq_bfs_instance g = a.graphs[(u32)gs];
+        g.src = (u32)(gs >> 32);
+        const u32 levels = cluster_bfs<KIND>(qa, qb, ctl + 1, g, dist, ct, nct, cluster, &edges);
+        if (ct == 0) {
+            ServeEntry* e = a.ring + (t & a.ring_mask);
+            __threadfence_system();
+            st_rlx_sys(&e->levels, levels);
+            st_rel_sys(&e->done, t + 1);
+            ++served;
+        }
+    }
+    warp_add_full(a.stats, edges);
+    if (ct == 0 && served) atomicAdd(a.stats + 1, served);
+}
+
+// ---------------------------------------------------------------------------
+// Host runtime
+// ---------------------------------------------------------------------------
+
+typedef std::chrono::steady_clock Clock;
+
+// First-fit allocator over [0, size) with coalescing of freed neighbours.
+class Arena {
+  public:
+    explicit Arena(u64 size) {
+        if (size) free_[0] = size;
+    }
+    bool alloc(u64 bytes, u64* off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            *off = it->first;
+            const u64 rest = it->second - bytes, at = it->first + bytes;
+            free_.erase(it);
+            if (rest) free_[at] = rest;
+            return true;
+        }
+        return false;
+    }
+    void release(u64 off, u64 bytes) {
+        auto nx = free_.lower_bound(off);
+        if (nx != free_.end() && off + bytes == nx->first) {
+            bytes += nx->second;
+            nx = free_.erase(nx);
+        }
+        if (nx != free_.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                pv->second += bytes;
+                return;
+            }
+        }
+        free_[off] = bytes;
+    }
+
+  private:
+    std::map<u64, u64> free_;
+};
+
+u64 round256(u64 b) { return (b + 255) / 256 * 256; }
+
+u64 ring_capacity_for(u64 n) {
+    u64 c = 4096;
+    while (c < n) c <<= 1;
+    return c;
+}
+u64 ymc_pool_for(u64 n) { return 4 * n + (1ull << 18); }
+
+// Queue capacity and thread count used for a graph of n vertices.
+u64 queue_capacity(int kind, u64 n) { return kind == GQ_YMC ? ymc_pool_for(n) : ring_capacity_for(n); }
+
+struct Runtime {
+    const gq_serve_config& c;
+    gq_serve_result& r;
+    std::vector<u64> charge, dist_bytes, arena_off;
+    std::vector<char> finished, waited;
+    Arena arena;
+    u64 charged = 0;
+    char* d_arena = nullptr;
+    Clock::time_point t0;
+
+    Runtime(const gq_serve_config& cfg, gq_serve_result& res, u64 arena_size)
+        : c(cfg), r(res), arena(arena_size) {}
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+
+    // Admits request i (charges the budget, places its distance array);
+    // false if it must wait.
+    bool admit(u64 i, u32** dist) {
+        if (charged + charge[i] > c.budget_bytes) return false;
+        uint32_t* out = c.req_out ? c.req_out[i] : nullptr;
+        if (!out) {
+            u64 off = 0;
+            if (!arena.alloc(dist_bytes[i], &off)) return false;
+            arena_off[i] = off;
+            out = reinterpret_cast<uint32_t*>(d_arena + off);
+        }
+        charged += charge[i];
+        if (charged > r.peak_state_bytes) r.peak_state_bytes = charged;
+        *dist = out;
+        return true;
+    }
+    void complete(u64 i, double t) {
+        r.latency_s[i] = t - c.req_arrival_s[i];
+        charged -= charge[i];
+        if (arena_off[i] != ~0ull) arena.release(arena_off[i], dist_bytes[i]);
+        finished[i] = 1;
+    }
+};
+
+struct Queues {
+    std::vector<gq_handle> h;
+    ~Queues() {
+        for (gq_handle q : h)
+            if (q) gq_destroy(q);
+    }
+    int create(u64 count, int kind, u64 cap, u32 max_threads, cudaStream_t st) {
+        h.assign(count, nullptr);
+        for (u64 i = 0; i < count; ++i) {
+            const int s = gq_create(kind, cap, 4, max_threads, nullptr, nullptr, st, &h[i]);
+            if (s != GQ_OK) return s;
+        }
+        return GQ_OK;
+    }
+    int status(cudaStream_t st) {
+        for (gq_handle q : h) {
+            const int s = gq_sync_status(q, st);
+            if (s != GQ_OK) return s;
+        }
+        return GQ_OK;
+    }
+};
+
+template <int KIND>
+cudaError_t launch_serve(u32 slots, u32 cb, const gq_dev* views, const ServeK& a, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(slots * cb);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cb;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_serve<KIND>, views, a);
+}
+
+template <int KIND>
+cudaError_t max_clusters(u32 cb, int* out) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cb);
+    cfg.blockDim = dim3(256);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cb;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(out, k_serve<KIND>, &cfg);
+}
+
+// RAII for the device and mapped allocations of one gq_serve call.
+struct Buffers {
+    void* dev = nullptr;      // claim, per-slot control words, stats, views, graphs
+    void* mapped = nullptr;   // ring + shared words
+    char* arena = nullptr;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> ev;
+    ~Buffers() {
+        if (st) cudaStreamSynchronize(st);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (dev) cudaFree(dev);
+        if (arena) cudaFree(arena);
+        if (mapped) cudaFreeHost(mapped);
+        if (st) cudaStreamDestroy(st);
+    }
+};
+
+int serve_persistent(Runtime& rt, Buffers& b, u64 nmax) {
+    const gq_serve_config& c = rt.c;
+    const u32 cb = c.cluster_blocks;
+    int fit = 0;
+    cudaError_t e = c.kind == GQ_LFQ ? max_clusters<GQ_LFQ>(cb, &fit)
+                    : c.kind == GQ_WFQ ? max_clusters<GQ_WFQ>(cb, &fit)
+                                       : max_clusters<GQ_YMC>(cb, &fit);
+    if (e != cudaSuccess || fit < 1) return GQ_ERR_CUDA;
+    u32 slots = c.slots ? c.slots : (u32)fit;
+    if (slots > (u32)fit) slots = (u32)fit;
+    if ((u64)slots > c.nrequests) slots = c.nrequests;
+    rt.r.slots_used = slots;
+
+    Queues fr;
+    int s = fr.create(2ull * slots, c.kind, queue_capacity(c.kind, nmax), cb * 256, b.st);
+    if (s != GQ_OK) return s;
+
+    u64 ring_n = 1;
+    while (ring_n < c.nrequests && ring_n < 4096) ring_n <<= 1;
+    const u64 ring_bytes = ring_n * sizeof(ServeEntry);
+    if (cudaHostAlloc(&b.mapped, ring_bytes + sizeof(ServeShared), cudaHostAllocMapped) != cudaSuccess)
+        return GQ_ERR_NOMEM;
+    std::memset(b.mapped, 0, ring_bytes + sizeof(ServeShared));
+    ServeEntry* ring = static_cast<ServeEntry*>(b.mapped);
+    ServeShared* sh = reinterpret_cast<ServeShared*>(static_cast<char*>(b.mapped) + ring_bytes);
+    void* d_mapped = nullptr;
+    if (cudaHostGetDevicePointer(&d_mapped, b.mapped, 0) != cudaSuccess) return GQ_ERR_CUDA;
+
+    // device block: claim (256 B) | ctl 64 B per slot | stats | views | graphs
+    const u64 o_ctl = 256, o_stats = round256(o_ctl + 64ull * slots), o_views = o_stats + 256,
+              o_graphs = round256(o_views + 2ull * slots * sizeof(gq_dev)),
+              total = round256(o_graphs + (u64)c.ngraphs * sizeof(gq_bfs_instance));
+    if (cudaMalloc(&b.dev, total) != cudaSuccess) return GQ_ERR_NOMEM;
+    char* d = static_cast<char*>(b.dev);
+    std::vector<gq_dev> views(2ull * slots);
+    for (u64 i = 0; i < views.size(); ++i) views[i] = fr.h[i]->dev;
+    if (cudaMemsetAsync(d, 0, o_views, b.st) != cudaSuccess ||
+        cudaMemcpyAsync(d + o_views, views.data(), views.size() * sizeof(gq_dev), cudaMemcpyHostToDevice, b.st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d + o_graphs, c.graphs, (u64)c.ngraphs * sizeof(gq_bfs_instance), cudaMemcpyHostToDevice,
+                        b.st) != cudaSuccess ||
+        cudaStreamSynchronize(b.st) != cudaSuccess)
+        return GQ_ERR_CUDA;
+
+    ServeK a;
+    a.ring = static_cast<ServeEntry*>(d_mapped);
+    a.sh = reinterpret_cast<ServeShared*>(static_cast<char*>(d_mapped) + ring_bytes);
+    a.graphs = reinterpret_cast<const gq_bfs_instance*>(d + o_graphs);
+    a.ngraphs = c.ngraphs;
+    a.ring_mask = (u32)(ring_n - 1);
+    a.nreq = c.nrequests;
+    a.claim = reinterpret_cast<u64*>(d);
+    a.ctl = reinterpret_cast<u64*>(d + o_ctl);
+    a.stats = reinterpret_cast<unsigned long long*>(d + o_stats);
+    const double limit = c.wait_limit_s > 0 ? c.wait_limit_s : 30.0;
+    a.wait_ns = (u64)(limit * 1e9);
+    const gq_dev* dv = reinterpret_cast<const gq_dev*>(d + o_views);
+    e = c.kind == GQ_LFQ ? launch_serve<GQ_LFQ>(slots, cb, dv, a, b.st)
+        : c.kind == GQ_WFQ ? launch_serve<GQ_WFQ>(slots, cb, dv, a, b.st)
+                           : launch_serve<GQ_YMC>(slots, cb, dv, a, b.st);
+    if (e != cudaSuccess) return GQ_ERR_CUDA;
+
+    rt.t0 = Clock::now();
+    const u64 n = c.nrequests;
+    u64 next = 0, done = 0;
+    std::vector<u64> inflight;
+    double last_progress = 0;
+    int err = GQ_OK;
+    for (u64 iter = 0; done < n; ++iter) {
+        double t = rt.now();
+        while (next < n && c.req_arrival_s[next] <= t) {
+            if (next >= ring_n && !rt.finished[next - ring_n]) break;   // ring entry still in use
+            u32* dist = nullptr;
+            if (!rt.admit(next, &dist)) {
+                if (!rt.waited[next]) {
+                    rt.waited[next] = 1;
+                    ++rt.r.admission_waits;
+                }
+                break;
+            }
+            ServeEntry* en = ring + (next & (ring_n - 1));
+            en->req = (u64)c.req_graph[next] | ((u64)c.req_src[next] << 32);
+            en->dist = reinterpret_cast<u64>(dist);
+            en->levels = 0;
+            __atomic_store_n(&en->seq, next + 1, __ATOMIC_RELEASE);
+            inflight.push_back(next);
+            ++next;
+        }
+        t = rt.now();
+        for (u64 k = 0; k < inflight.size();) {
+            const u64 i = inflight[k];
+            ServeEntry* en = ring + (i & (ring_n - 1));
+            if (__atomic_load_n(&en->done, __ATOMIC_ACQUIRE) == i + 1) {
+                rt.complete(i, t);
+                ++done;
+                last_progress = t;
+                if (en->levels == ~0ull && err == GQ_OK) err = GQ_ERR_INVALID;
+                inflight[k] = inflight.back();
+                inflight.pop_back();
+            } else {
+                ++k;
+            }
+        }
+        if (done == n) break;
+        if ((iter & 1023) == 1023) {
+            const cudaError_t q = cudaStreamQuery(b.st);
+            if (q != cudaErrorNotReady) {   // the scheduler ended with requests outstanding
+                err = q != cudaSuccess ? GQ_ERR_CUDA : GQ_ERR_TIMEOUT;
+                break;
+            }
+            const double waiting_since = next < n && c.req_arrival_s[next] > last_progress ? c.req_arrival_s[next]
+                                                                                              : last_progress;
+            if (inflight.size() && t - waiting_since > limit + 5.0) {
+                err = GQ_ERR_TIMEOUT;
+                break;
+            }
+        }
+    }
+    __atomic_store_n(&sh->stop, 1ull, __ATOMIC_RELEASE);
+    if (cudaStreamSynchronize(b.st) != cudaSuccess) return GQ_ERR_CUDA;
+    unsigned long long st2[3] = {0, 0, 0};
+    if (cudaMemcpy(st2, d + o_stats, sizeof(st2), cudaMemcpyDeviceToHost) != cudaSuccess) return GQ_ERR_CUDA;
+    if (st2[2]) return st2[2] == 2 ? GQ_ERR_INVALID : GQ_ERR_TIMEOUT;
+    if (err != GQ_OK) return err;
+    rt.r.edges_scanned = st2[0];
+    if (st2[1] != n) return GQ_ERR_TIMEOUT;
+    return fr.status(b.st);
+}
+
+int serve_per_request(Runtime& rt, Buffers& b, u64 nmax) {
+    const gq_serve_config& c = rt.c;
+    Queues fr;
+    // gq_bfs runs one thread per resident slot of the GPU (at most max_threads)
+    int s = fr.create(2, c.kind, queue_capacity(c.kind, nmax), 1u << 19, b.st);
+    if (s != GQ_OK) return s;
+    if (cudaStreamSynchronize(b.st) != cudaSuccess) return GQ_ERR_CUDA;
+    const u64 n = c.nrequests;
+    const u64 nev = n < 1024 ? n : 1024;
+    b.ev.assign(nev, nullptr);
+    for (u64 i = 0; i < nev; ++i)
+        if (cudaEventCreateWithFlags(&b.ev[i], cudaEventDisableTiming) != cudaSuccess) return GQ_ERR_CUDA;
+
+    rt.t0 = Clock::now();
+    const double limit = c.wait_limit_s > 0 ? c.wait_limit_s : 30.0;
+    u64 next = 0, done = 0;
+    double last_progress = 0;
+    while (done < n) {
+        double t = rt.now();
+        while (next < n && c.req_arrival_s[next] <= t && next - done < nev) {
+            u32* dist = nullptr;
+            if (!rt.admit(next, &dist)) {
+                if (!rt.waited[next]) {
+                    rt.waited[next] = 1;
+                    ++rt.r.admission_waits;
+                }
+                break;
+            }
+            const gq_bfs_instance& g = c.graphs[c.req_graph[next]];
+            if (c.kind == GQ_YMC && (gq_reset(fr.h[0], b.st) != GQ_OK || gq_reset(fr.h[1], b.st) != GQ_OK))
+                return GQ_ERR_CUDA;
+            s = gq_bfs(fr.h[0], fr.h[1], g.n, g.d_offsets, g.d_adj, c.req_src[next], dist, nullptr, b.st);
+            if (s != GQ_OK) return s;
+            if (cudaEventRecord(b.ev[next % nev], b.st) != cudaSuccess) return GQ_ERR_CUDA;
+            ++next;
+        }
+        // one stream: requests complete in submission order
+        while (done < next) {
+            const cudaError_t q = cudaEventQuery(b.ev[done % nev]);
+            if (q == cudaErrorNotReady) break;
+            if (q != cudaSuccess) return GQ_ERR_CUDA;
+            t = rt.now();
+            rt.complete(done, t);
+            ++done;
+            last_progress = t;
+        }
+        if (done < next && rt.now() - last_progress > limit + 5.0 &&
+            rt.now() - c.req_arrival_s[done] > limit + 5.0)
+            return GQ_ERR_TIMEOUT;
+    }
+    if (cudaStreamSynchronize(b.st) != cudaSuccess) return GQ_ERR_CUDA;
+    return fr.status(b.st);
+}
+
+int validate(const gq_serve_config* c, const gq_serve_result* r) {
+    if (!c || !r || !r->latency_s) return GQ_ERR_INVALID;
+    if (c->kind != GQ_LFQ && c->kind != GQ_WFQ && c->kind != GQ_YMC) return GQ_ERR_INVALID;
+    if (c->mode != GQ_SERVE_PERSISTENT && c->mode != GQ_SERVE_PER_REQUEST) return GQ_ERR_INVALID;
+    if (c->mode == GQ_SERVE_PERSISTENT && c->cluster_blocks != 1 && c->cluster_blocks != 2 &&
+        c->cluster_blocks != 4 && c->cluster_blocks != 8)
+        return GQ_ERR_INVALID;
+    if (!c->ngraphs || !c->nrequests || !c->graphs || !c->req_graph || !c->req_src || !c->req_arrival_s)
+        return GQ_ERR_INVALID;
+    if (!(c->wait_limit_s >= 0) || c->budget_bytes == 0) return GQ_ERR_INVALID;
+    for (u32 g = 0; g < c->ngraphs; ++g) {
+        const gq_bfs_instance& x = c->graphs[g];
+        if (x.n == 0 || x.n >= 0xFFFFFFFFull || !x.d_offsets || !x.d_adj) return GQ_ERR_INVALID;
+    }
+    for (u32 i = 0; i < c->nrequests; ++i) {
+        if (c->req_graph[i] >= c->ngraphs || c->req_src[i] >= c->graphs[c->req_graph[i]].n) return GQ_ERR_INVALID;
+        if (!(c->req_arrival_s[i] >= 0) || (i && c->req_arrival_s[i] < c->req_arrival_s[i - 1]))
+            return GQ_ERR_INVALID;
+    }
+    return GQ_OK;
+}
+
+}  // namespace
+
+extern "C" int gq_serve(const gq_serve_config* cfg, gq_serve_result* res) {
+    int s = validate(cfg, res);
+    if (s != GQ_OK) return s;
+    const gq_serve_config& c = *cfg;
+    res->wall_s = 0;
+    res->peak_state_bytes = res->admission_waits = res->edges_scanned = 0;
+    res->slots_used = 0;
+    res->status = GQ_OK;
+    for (u32 i = 0; i < c.nrequests; ++i) res->latency_s[i] = -1.0;
+
+    // per-graph state: CSR bytes need m = offsets[n], read once from the device
+    std::vector<u64> graph_charge(c.ngraphs), graph_dist(c.ngraphs);
+    u64 nmax = 1;
+    const u32 mt = c.mode == GQ_SERVE_PERSISTENT ? c.cluster_blocks * 256 : (1u << 19);
+    for (u32 g = 0; g < c.ngraphs; ++g) {
+        const gq_bfs_instance& x = c.graphs[g];
+        u64 m = 0;
+        if (cudaMemcpy(&m, x.d_offsets + x.n, sizeof(u64), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return res->status = GQ_ERR_CUDA;
+        uint64_t qb = 0;
+        s = gq_workspace_bytes(c.kind, queue_capacity(c.kind, x.n), 4, mt, nullptr, &qb);
+        if (s != GQ_OK) return res->status = s;
+        graph_dist[g] = round256(4 * x.n);
+        graph_charge[g] = 8 * (x.n + 1) + 4 * m + graph_dist[g] + 2 * qb;
+        if (x.n > nmax) nmax = x.n;
+    }
+    u64 arena_need = 0;
+    for (u32 i = 0; i < c.nrequests; ++i) {
+        const u32 g = c.req_graph[i];
+        if (graph_charge[g] > c.budget_bytes) return res->status = GQ_ERR_INVALID;
+        if (!c.req_out || !c.req_out[i]) arena_need += graph_dist[g];
+    }
+    const u64 arena_size = arena_need < c.budget_bytes ? arena_need : c.budget_bytes;
+    Runtime rt(c, *res, arena_size);
+    rt.charge.resize(c.nrequests);
+    rt.dist_bytes.resize(c.nrequests);
+    rt.arena_off.assign(c.nrequests, ~0ull);
+    rt.finished.assign(c.nrequests, 0);
+    rt.waited.assign(c.nrequests, 0);
+    for (u32 i = 0; i < c.nrequests; ++i) {
+        rt.charge[i] = graph_charge[c.req_graph[i]];
+        rt.dist_bytes[i] = graph_dist[c.req_graph[i]];
+    }
+
+    Buffers b;
+    if (cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking) != cudaSuccess) return res->status = GQ_ERR_CUDA;
+    if (arena_size && cudaMalloc(&b.arena, arena_size) != cudaSuccess) return res->status = GQ_ERR_NOMEM;
+    rt.d_arena = b.arena;
+    s = c.mode == GQ_SERVE_PERSISTENT ? serve_persistent(rt, b, nmax) : serve_per_request(rt, b, nmax);
+    double last = 0;
+    for (u32 i = 0; i < c.nrequests; ++i)
+        if (rt.finished[i] && c.req_arrival_s[i] + res->latency_s[i] > last)
+            last = c.req_arrival_s[i] + res->latency_s[i];
+    res->wall_s = last - c.req_arrival_s[0];
+    return res->status = s;
+}

@@ -207,6 +207,42 @@ def bfs_sources(offsets: np.ndarray, seed: int, count: int = 3) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# Serving workload: a pool of R-MAT graphs and a stream of BFS requests
+# ---------------------------------------------------------------------------
+
+def _unit(seed: int, ctr) -> np.ndarray:
+    """Uniform doubles in [0, 1) with 53 random bits."""
+    return (splitmix64(seed, ctr) >> np.uint64(11)).astype(np.float64) * 2.0**-53
+
+
+def rmat_pool_scales(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """Scales of a graph pool, uniform integers in [lo, hi] (a log-uniform vertex count)."""
+    return lo + np.minimum((_unit(seed, np.arange(count)) * (hi - lo + 1)).astype(np.int64), hi - lo)
+
+
+def serving_requests(offsets_list, count: int, rate: float, seed: int):
+    """`count` BFS requests over the graphs whose CSR offsets are listed.
+
+    Graph id uniform over the pool; source the first of up to 64 uniform draws
+    with degree > 0 (vertex 0 if none); Poisson arrivals at `rate` per second,
+    the first at 0, then exponential gaps -ln(1 - u) / rate.
+    Returns (graph ids uint32, sources uint32, arrival offsets float64 seconds)."""
+    ng = len(offsets_list)
+    gid = np.minimum((_unit(seed, np.arange(count)) * ng).astype(np.int64), ng - 1)
+    src = np.zeros(count, dtype=np.uint32)
+    for i in range(count):
+        off = offsets_list[gid[i]]
+        n = len(off) - 1
+        draws = splitmix64(seed + 1, np.arange(64, dtype=np.uint64) + np.uint64(64 * i)) % np.uint64(n)
+        deg = off[draws.astype(np.int64) + 1] - off[draws.astype(np.int64)]
+        hit = np.flatnonzero(deg > 0)
+        src[i] = int(draws[hit[0]]) if hit.size else 0
+    gaps = -np.log1p(-_unit(seed + 2, np.arange(count))) / float(rate)
+    arrival = np.concatenate([[0.0], np.cumsum(gaps[1:])])
+    return gid.astype(np.uint32), src, arrival
+
+
+# ---------------------------------------------------------------------------
 # Ray-tracing scene: spheres in the unit box
 # ---------------------------------------------------------------------------
 

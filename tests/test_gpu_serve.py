@@ -1,0 +1,130 @@
+"""Serving on the GPU (run with -m gpu): BFS requests served by the persistent
+device scheduler (host request ring in mapped pinned memory) and by one launch
+per request.  Every request's distances must equal the oracle's sequential
+BFS, and be the same whether the request is served alone or in the mix."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2606_01693_gb300 as gq
+import synth
+
+pytestmark = pytest.mark.gpu
+KINDS = list(gq.READY_KINDS)
+MODES = ["persistent", "per_request"]
+
+
+@pytest.fixture(scope="module")
+def pool():
+    host = [synth.rmat_csr_fast(int(s), seed=900 + i) for i, s in enumerate([6, 8, 9, 10, 11, 12])]
+    host.append(synth.grid_csr(48, 20))      # a deep graph: 66 levels
+    dev = [(torch.from_numpy(o.view(np.int64)).cuda(), torch.from_numpy(a.view(np.int32)).cuda()) for o, a in host]
+    return host, dev
+
+
+def _expected(host, gid, src):
+    memo = {}
+    out = []
+    for g, s in zip(gid, src):
+        key = (int(g), int(s))
+        if key not in memo:
+            memo[key] = oracle.bfs(host[g][0], host[g][1], int(s))
+        out.append(memo[key])
+    return out
+
+
+def _outs(host, gid):
+    return [torch.empty(len(host[g][0]) - 1, dtype=torch.int32, device="cuda") for g in gid]
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("mode", MODES)
+def test_mix_matches_cpu_bfs(pool, kind, mode):
+    host, dev = pool
+    gid, src, arr = synth.serving_requests([h[0] for h in host], 48, 4000.0, seed=21)
+    outs = _outs(host, gid)
+    r = gq.gq_serve(kind, dev, gid, src, arr, mode=mode, slots=6, cluster_blocks=2, outs=outs)
+    torch.cuda.synchronize()
+    assert (r["latency_s"] >= 0).all()
+    assert r["wall_s"] >= r["latency_s"][-1] - 1e-9
+    want = _expected(host, gid, src)
+    for o, w in zip(outs, want):
+        assert (o.cpu().numpy().view(np.uint32) == w).all()
+    if mode == "persistent":
+        assert r["slots_used"] == 6
+        reached_edges = sum(int(np.diff(host[g][0].astype(np.int64))[w != 0xFFFFFFFF].sum())
+                            for g, w in zip(gid, want))
+        assert r["edges_scanned"] == reached_edges
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_alone_equals_in_mix(pool, kind):
+    """Each request served alone gives the bytes it gave in the mix (both modes)."""
+    host, dev = pool
+    gid, src, arr = synth.serving_requests([h[0] for h in host], 24, 20000.0, seed=33)
+    mix = {}
+    for mode in MODES:
+        outs = _outs(host, gid)
+        gq.gq_serve(kind, dev, gid, src, arr, mode=mode, slots=8, cluster_blocks=4, outs=outs)
+        mix[mode] = [o.cpu().numpy() for o in outs]
+    for i in range(0, 24, 3):
+        o = _outs(host, gid[i:i + 1])
+        gq.gq_serve(kind, dev, gid[i:i + 1], src[i:i + 1], [0.0], mode="persistent", slots=1, cluster_blocks=1,
+                    outs=o)
+        alone = o[0].cpu().numpy()
+        assert (alone == mix["persistent"][i]).all()
+        assert (alone == mix["per_request"][i]).all()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_admission_waits_under_small_budget(pool, mode):
+    """With room for about two requests' state, later requests wait; results stay exact."""
+    host, dev = pool
+    gid, src, arr = synth.serving_requests([h[0] for h in host], 40, 1e6, seed=5)   # a burst
+    def charge(g):
+        n, m = len(host[g][0]) - 1, int(host[g][0][-1])
+        qb = gq.gq_workspace_bytes(gq.GQ_LFQ, max(4096, 1 << (n - 1).bit_length()), 4,
+                                   512 if mode == "persistent" else 1 << 19)
+        return 8 * (n + 1) + 4 * m + (4 * n + 255) // 256 * 256 + 2 * qb
+    budget = int(2.2 * max(charge(int(g)) for g in set(gid.tolist())))
+    r = gq.gq_serve("lfq", dev, gid, src, arr, mode=mode, slots=8, cluster_blocks=2, budget_bytes=budget)
+    assert r["peak_state_bytes"] <= budget
+    assert r["admission_waits"] > 0
+    assert (r["latency_s"] >= 0).all()
+    outs = _outs(host, gid)
+    r = gq.gq_serve("lfq", dev, gid, src, arr, mode=mode, slots=8, cluster_blocks=2, budget_bytes=budget,
+                    outs=outs)
+    for o, w in zip(outs, _expected(host, gid, src)):
+        assert (o.cpu().numpy().view(np.uint32) == w).all()
+
+
+def test_request_larger_than_budget_rejected(pool):
+    host, dev = pool
+    with pytest.raises(gq.GqError) as ei:
+        gq.gq_serve("lfq", dev, [5], [0], [0.0], budget_bytes=1 << 16)
+    assert ei.value.status == gq.GQ_ERR_INVALID
+
+
+def test_ring_wraps(pool):
+    """More requests than ring entries (4096): entries are reused once their request is done."""
+    host, dev = pool
+    small = [host[0], host[1]]
+    gid, src, arr = synth.serving_requests([h[0] for h in small], 5000, 2e5, seed=8)
+    r = gq.gq_serve("lfq", [dev[0], dev[1]], gid, src, arr, mode="persistent", slots=16, cluster_blocks=1)
+    assert (r["latency_s"] >= 0).all()
+    want = _expected(small, gid, src)
+    edges = sum(int(np.diff(small[g][0].astype(np.int64))[w != 0xFFFFFFFF].sum()) for g, w in zip(gid, want))
+    assert r["edges_scanned"] == edges
+
+
+def test_device_wait_limit_reports_timeout(pool):
+    """A scheduler cluster whose next request arrives after the wait limit gives up
+    (bounded %globaltimer wait) and the call returns GQ_ERR_TIMEOUT; the context stays usable."""
+    host, dev = pool
+    with pytest.raises(gq.GqError) as ei:
+        gq.gq_serve("lfq", dev, [0, 1], [0, 0], [0.0, 3.0], mode="persistent", slots=2, cluster_blocks=1,
+                    wait_limit_s=0.3)
+    assert ei.value.status == gq.GQ_ERR_TIMEOUT
+    r = gq.gq_serve("lfq", dev, [0], [0], [0.0], mode="persistent", slots=1, cluster_blocks=1)
+    assert r["latency_s"][0] >= 0

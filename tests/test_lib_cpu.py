@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared_symbols():
     names = set()
-    for h in ("gq.h", "gq_drivers.h", "gq_apps.h"):
+    for h in ("gq.h", "gq_drivers.h", "gq_apps.h", "gq_serve.h"):
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         for m in re.finditer(r"^\s*(?:int|const char\*|void)\s+(gq_\w+)\s*\(", src, flags=re.M):
@@ -83,3 +83,35 @@ def test_workspace_grows_with_capacity_and_records():
     assert y >= 3 * 1001 * 8 + 256 * 128
     for v in (a, b, w1, w2, y):
         assert v % 256 == 0
+
+
+def _serve_cfg(**kw):
+    """A serving configuration with fake device addresses (only validated, never dereferenced)."""
+    import numpy as np
+    g = (gq.gq_bfs_instance * 2)(gq.gq_bfs_instance(100, 0x10000, 0x20000, None, 0, 0),
+                                 gq.gq_bfs_instance(50, 0x30000, 0x40000, None, 0, 0))
+    rg = np.array(kw.pop("req_graph", [0, 1, 0]), dtype=np.uint32)
+    rs = np.array(kw.pop("req_src", [3, 49, 99]), dtype=np.uint32)
+    ra = np.array(kw.pop("arrival", [0.0, 0.1, 0.2]), dtype=np.float64)
+    keep = [g, rg, rs, ra]
+    cfg = gq.gq_serve_config(kind=kw.pop("kind", 0), mode=kw.pop("mode", 0), slots=0,
+                             cluster_blocks=kw.pop("cluster_blocks", 2), budget_bytes=kw.pop("budget", 1 << 30),
+                             wait_limit_s=kw.pop("wait", 0.0), ngraphs=kw.pop("ngraphs", 2), nrequests=len(rg),
+                             graphs=ctypes.cast(g, ctypes.c_void_p).value, req_graph=rg.ctypes.data,
+                             req_src=rs.ctypes.data, req_arrival_s=ra.ctypes.data, req_out=None)
+    lat = np.zeros(len(rg))
+    res = gq.gq_serve_result(latency_s=lat.ctypes.data)
+    keep.append(lat)
+    return cfg, res, keep
+
+
+@pytest.mark.parametrize("change", [
+    {"kind": 7}, {"mode": 2}, {"cluster_blocks": 3}, {"req_graph": [0, 2, 0]}, {"req_src": [3, 50, 99]},
+    {"arrival": [0.0, 0.2, 0.1]}, {"arrival": [0.0, float("nan"), 0.2]}, {"budget": 0}, {"wait": -1.0},
+    {"ngraphs": 0},
+])
+def test_serve_rejects_bad_config(change):
+    cfg, res, keep = _serve_cfg(**change)
+    assert gq.load().gq_serve(ctypes.byref(cfg), ctypes.byref(res)) == gq.GQ_ERR_INVALID
+    assert gq.load().gq_serve(None, ctypes.byref(res)) == gq.GQ_ERR_INVALID
+    assert gq.load().gq_serve(ctypes.byref(cfg), None) == gq.GQ_ERR_INVALID
