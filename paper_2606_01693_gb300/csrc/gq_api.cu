@@ -373,10 +373,11 @@ extern "C" int gq_create(int kind, uint64_t capacity, uint32_t elem_bytes, uint3
 extern "C" int gq_destroy(gq_handle h) {
     if (!h) return GQ_ERR_INVALID;
     int s = GQ_OK;
-    if (h->owned) {
+    if (h->owned || h->aux) {
         if (cudaDeviceSynchronize() != cudaSuccess) s = GQ_ERR_CUDA;
-        if (cudaFree(h->ws) != cudaSuccess) s = GQ_ERR_CUDA;
     }
+    if (h->owned && cudaFree(h->ws) != cudaSuccess) s = GQ_ERR_CUDA;
+    if (h->aux && cudaFree(h->aux) != cudaSuccess) s = GQ_ERR_CUDA;
     delete h;
     return s;
 }

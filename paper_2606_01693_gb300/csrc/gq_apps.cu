@@ -24,6 +24,7 @@ using namespace gqd;
 namespace {
 
 constexpr u32 kBarrierSpinLimit = 1u << 26;   // x ~100 ns sleeps: a few seconds
+constexpr u64 kGridChunkCap = 1u << 21;       // chunk-map positions of a whole-GPU search
 
 // Control words in the first queue's scratch line (words 8..15).
 enum { kCtlBarCount = 0, kCtlBarGen = 1, kCtlFront0 = 2, kCtlFront1 = 3, kCtlFront2 = 4, kCtlErr = 5 };
@@ -62,13 +63,14 @@ __device__ __forceinline__ bool grid_barrier(u64* ctl, u32 nblocks) {
 template <int KIND>
 __global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, const __grid_constant__ gq_dev qb, u64 n,
                                              const u64* __restrict__ off, const u32* __restrict__ adj, u32 src,
-                                             u32* dist, unsigned long long* stats) {
+                                             u32* dist, u64* table, u64 cap, unsigned long long* stats) {
     u64* ctl = reinterpret_cast<u64*>(qa.scratch) + 8;
     const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
     const u32 nthreads = gridDim.x * blockDim.x;
-    const u32 lane = threadIdx.x & 31;
-    const u32 warp = tid >> 5;
+    const u32 warp = tid >> 5, nwarps = nthreads >> 5;
     for (u64 v = tid; v < n; v += nthreads) dist[v] = kUnreached;
+    if (tid == 0)
+        for (u32 w = 0; w < 9; ++w) st_rlx(table + w, 0);
     if (!grid_barrier(ctl, gridDim.x)) return;
     if (tid == 0) {
         dist[src] = 0;
@@ -81,41 +83,19 @@ __global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, 
         const u64 frontier = ld_acq(ctl + kCtlFront0 + level % 3);
         if (frontier == 0) break;
         reached += (tid == 0) ? frontier : 0;
-        if (tid == 0) st_rlx(ctl + kCtlFront0 + (level + 2) % 3, 0);   // read by all during level - 1
+        if (tid == 0) {
+            st_rlx(ctl + kCtlFront0 + (level + 2) % 3, 0);   // read by all during level - 1
+            chunk_prepare_next(table, level);
+        }
+        const u64 want = (frontier + 31) / 32;
+        const u64 dq = want < nwarps ? want : nwarps;
+        const LevelCtx c = level_ctx(off, adj, dist, level, tid, table, cap, dq);
         const gq_dev& cur = (level & 1) ? qb : qa;
         const gq_dev& nxt = (level & 1) ? qa : qb;
         u32 cnt = 0;
-        const u64 want = (frontier + 31) / 32;
-        if (warp < want || warp < 1) {
-            bool active = true;
-            for (u32 round = 0; round < kRetryLimit; ++round) {
-                unsigned int v = 0;
-                int s = GQ_EMPTY;
-                if (active) s = queue_dequeue<unsigned int, KIND>(cur, &v, tid);
-                active = active && (s == GQ_OK);   // an EMPTY is final within a level
-                const u32 got = __ballot_sync(0xffffffffu, active);
-                if (!got) break;
-                u64 b = 0, e = 0;
-                if (active) {
-                    b = off[v];
-                    e = off[v + 1];
-                    if (e - b < 32) {                 // low degree: this lane alone
-                        edges += e - b;
-                        for (u64 k = b; k < e; ++k) bfs_visit<KIND>(nxt, dist, adj[k], level + 1, tid, &cnt);
-                    }
-                }
-                u32 big = __ballot_sync(0xffffffffu, active && (e - b >= 32));
-                while (big) {                         // high degree: the whole warp, coalesced
-                    const u32 owner = __ffs(big) - 1;
-                    big &= big - 1;
-                    const u64 bb = __shfl_sync(0xffffffffu, b, owner);
-                    const u64 ee = __shfl_sync(0xffffffffu, e, owner);
-                    if (lane == 0) edges += ee - bb;
-                    for (u64 k = bb + lane; k < ee; k += 32) bfs_visit<KIND>(nxt, dist, adj[k], level + 1, tid, &cnt);
-                    __syncwarp();
-                }
-            }
-        }
+        if (warp < dq) level_dequeue<KIND>(cur, nxt, c, &cnt, &edges);
+        if (!level_chunks<KIND>(nxt, c, &cnt, &edges) && (threadIdx.x & 31) == 0)
+            atomicCAS(reinterpret_cast<unsigned long long*>(ctl + kCtlErr), 0ull, 2ull);
         warp_add_full(reinterpret_cast<unsigned long long*>(ctl + kCtlFront0 + (level + 1) % 3), cnt);
         if (!grid_barrier(ctl, gridDim.x)) return;
     }
@@ -139,10 +119,24 @@ int launch_bfs(gq_handle ha, gq_handle hb, uint64_t n, const uint64_t* off, cons
         if (grid > rec / 256) grid = rec / 256;
     }
     if (grid < 1) return GQ_ERR_TOO_MANY_THREADS;
+    // chunk map, owned by the first queue's handle (made and zeroed once; a
+    // search leaves it zeroed)
+    u64 cap = kGridChunkCap;
+    if (!ha->aux) {
+        const u64 bytes = chunk_map_bytes(cap);
+        if (cudaMalloc(&ha->aux, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            ha->aux = nullptr;
+            return GQ_ERR_NOMEM;
+        }
+        if (cudaMemsetAsync(ha->aux, 0, bytes, st) != cudaSuccess) return GQ_ERR_CUDA;
+        ha->aux_bytes = bytes;
+    }
+    u64* table = static_cast<u64*>(ha->aux);
     gq_dev qa = ha->dev, qb = hb->dev;
     const u64* o = reinterpret_cast<const u64*>(off);
     const u32* a = reinterpret_cast<const u32*>(adj);
-    void* args[] = {&qa, &qb, &n, (void*)&o, (void*)&a, &src, &dist, &stats};
+    void* args[] = {&qa, &qb, &n, (void*)&o, (void*)&a, &src, &dist, &table, &cap, &stats};
     if (cudaLaunchCooperativeKernel((const void*)k_bfs<KIND>, dim3((unsigned)grid), dim3(256), args, 0, st) != cudaSuccess)
         return GQ_ERR_CUDA;
     return gq_check_launch();
@@ -159,6 +153,7 @@ struct BatchK {
     const u32* order;
     u32 ninst;
     u64* ctl;                  // 8 words per slot: [0] instance, [1..3] frontier counts
+    u64* tables;               // chunk map per slot (kClusterChunkCap positions)
     unsigned long long* stats; // instances, edges, levels, errors
 };
 
@@ -191,7 +186,9 @@ __global__ void __launch_bounds__(256) k_bfs_batch(const __grid_constant__ gq_de
         cluster.sync();                      // everyone has read the id before ctl is reused
         if (id == kNoInstance || id >= a.ninst) break;
         const gq_bfs_instance g = a.inst[id];
-        const u32 lv = cluster_bfs<KIND>(qa, qb, ctl + 1, g, g.d_dist, ct, nct, cluster, &edges);
+        const u32 lv = cluster_bfs<KIND>(qa, qb, ctl + 1, a.tables + slot * (chunk_map_bytes(kClusterChunkCap) / 8),
+                                         kClusterChunkCap, g, g.d_dist, ct, nct, cluster, &edges,
+                                         a.stats ? a.stats + 3 : nullptr);
         if (ct == 0) {
             levels_sum += lv;
             ++done;
@@ -216,9 +213,11 @@ int launch_bfs_batch(gq_handle idq, const gq_handle* fr, u32 slots, u32 cb, cons
     for (u32 i = 0; i < 2 * slots; ++i) h[i] = fr[i]->dev;
     if (cudaMemcpyAsync(views, h.data(), h.size() * sizeof(gq_dev), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return GQ_ERR_CUDA;
-    if (cudaMemsetAsync(ctl, 0, (u64)slots * 64, st) != cudaSuccess) return GQ_ERR_CUDA;
+    u64* tables = ctl + 8 * (u64)slots;
+    if (cudaMemsetAsync(ctl, 0, (u64)slots * (64 + chunk_map_bytes(kClusterChunkCap)), st) != cudaSuccess)
+        return GQ_ERR_CUDA;
     k_bfs_batch_fill<<<1, 1, 0, st>>>(idq->dev, order, ninst, stats ? reinterpret_cast<u64*>(stats + 3) : ctl);
-    BatchK a{inst, order, ninst, ctl, stats};
+    BatchK a{inst, order, ninst, ctl, tables, stats};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(slots * cb);
     cfg.blockDim = dim3(256);
@@ -240,7 +239,8 @@ int launch_bfs_batch(gq_handle idq, const gq_handle* fr, u32 slots, u32 cb, cons
 
 extern "C" int gq_bfs_batch_workspace_bytes(uint32_t slots, uint64_t* bytes) {
     if (!slots || !bytes) return GQ_ERR_INVALID;
-    *bytes = (((uint64_t)2 * slots * sizeof(gq_dev) + 255) / 256) * 256 + (uint64_t)slots * 64;
+    *bytes = (((uint64_t)2 * slots * sizeof(gq_dev) + 255) / 256) * 256 +
+             (uint64_t)slots * (64 + chunk_map_bytes(kClusterChunkCap));
     return GQ_OK;
 }
 

@@ -40,19 +40,228 @@ __device__ inline void ymc_cluster_clear(const gq_dev& q, u32 ct, u32 nct, cg::c
     }
 }
 
-// One level-synchronous BFS by the threads of a thread-block cluster on the
-// frontier queues qa / qb (left empty).  ctl[0..2]: rotating frontier counts.
-// Returns the number of levels; adds scanned edges to *edges.
+// ---------------------------------------------------------------------------
+// Work of one warp in one level
+// ---------------------------------------------------------------------------
+//
+// Degrees are skewed (R-MAT hubs have 10^5 neighbours), so neither "the lane
+// that dequeued a vertex scans it" nor "its warp scans it" bounds the time of a
+// level.  Two mechanisms share the edges instead:
+//   * gather: a warp lays the adjacency lists of the (up to 32) vertices it
+//     dequeued end to end (warp prefix sum of their degrees) and scans the
+//     combined list 32 edges at a time, each lane finding its vertex by binary
+//     search over the prefix sums;
+//   * chunk map: a vertex of degree >= kHeavyDeg is cut into chunks of kChunk
+//     edges.  Its lane reserves that many consecutive map positions (one
+//     fetch-add on the level's `reserved` counter) and writes one word per
+//     chunk (vertex, chunk index).  Every warp of the search -- those with
+//     nothing to dequeue from the start, the others once their dequeues
+//     return EMPTY -- takes map positions with a fetch-add on `handed`,
+//     waits for the word at its position, scans that chunk and clears the
+//     word.  A warp leaves when the dequeuing warps are all done (`done`
+//     reached the number of dequeuing warps) and no reserved position is left.
+// Positions past the map's capacity are not written: the vertex is gathered
+// instead (the part of its reservation inside the map is written as skips).
+
+constexpr u64 kHeavyDeg = 128;
+constexpr u64 kChunk = 128;
+constexpr u32 kFull = 0xffffffffu;
+constexpr u64 kSkipChunk = ~0ull;
+constexpr u64 kChunkWaitNs = 4000000000ull;     // bound of any wait for a chunk word (4 s)
+constexpr u64 kClusterChunkCap = 1u << 14;      // chunk-map positions of one cluster's search
+
+// Map memory: 16 header words, per level rotating by 3: reserved [0..2],
+// handed [3..5], done [6..8]; then the map itself, cap words, all zero
+// between levels (every written word is cleared by the warp that scans it).
+// A map word is (vertex << 32) | (chunk index + 1), or kSkipChunk.
+__host__ __device__ constexpr u64 chunk_map_bytes(u64 cap) { return (16 + cap) * sizeof(u64); }
+
+struct LevelCtx {
+    const u64* off;
+    const u32* adj;
+    u32* dist;
+    u32 next_level, rec;    // rec: record id for the queue operations
+    u64* map;
+    u64 cap;
+    u64* reserved;
+    u64* handed;
+    u64* done;
+    u64 dequeuers;          // warps that dequeue this level
+};
+
+__device__ __forceinline__ LevelCtx level_ctx(const u64* off, const u32* adj, u32* dist, u32 level, u32 rec,
+                                              u64* table, u64 cap, u64 dequeuers) {
+    LevelCtx c;
+    c.off = off;
+    c.adj = adj;
+    c.dist = dist;
+    c.next_level = level + 1;
+    c.rec = rec;
+    c.map = table + 16;
+    c.cap = cap;
+    c.reserved = table + level % 3;
+    c.handed = table + 3 + level % 3;
+    c.done = table + 6 + level % 3;
+    c.dequeuers = dequeuers;
+    return c;
+}
+
+// Called by one thread during level L: clears the counters of level L + 1
+// (last used during level L - 2).
+__device__ __forceinline__ void chunk_prepare_next(u64* table, u32 level) {
+    const u32 r = (level + 1) % 3;
+    st_rlx(table + r, 0);
+    st_rlx(table + 3 + r, 0);
+    st_rlx(table + 6 + r, 0);
+}
+
+// Warp: scans the adjacency lists [b, b + d) of its lanes as one combined list.
 template <int KIND>
-__device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, const gq_bfs_instance& g, u32* dist, u32 ct,
-                           u32 nct, cg::cluster_group& cluster, u64* edges) {
+__device__ void warp_gather(const gq_dev& nxt, const LevelCtx& c, u64 b, u64 d, u32* cnt, u64* edges) {
     const u32 lane = threadIdx.x & 31;
-    const u32 cw = ct >> 5;
+    u64 incl = d;
+    for (u32 o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const u64 total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+    if (lane == 0) *edges += total;
+    const u64 start = b - (incl - d);   // combined index x of this lane's list is edge start + x (mod 2^64)
+    for (u64 base = 0; base < total; base += 32) {
+        const u64 x = base + lane;
+        u32 pos = 0;                     // first lane whose inclusive sum exceeds x
+        for (u32 step = 16; step; step >>= 1) {
+            const u64 v = __shfl_sync(kFull, incl, pos + step - 1);
+            if (v <= x) pos += step;
+        }
+        const u64 st = __shfl_sync(kFull, start, pos);
+        if (x < total) bfs_visit<KIND>(nxt, c.dist, c.adj[st + x], c.next_level, c.rec, cnt);
+    }
+}
+
+// Lane: cuts vertex v (edges [b, b + d)) into chunks and writes them into the
+// map; false if the map has no room (the caller gathers it).
+__device__ __forceinline__ bool chunk_publish(const LevelCtx& c, u32 v, u64 d) {
+    const u64 n = (d + kChunk - 1) / kChunk;
+    const u64 p = faa_rlx(c.reserved, n);
+    const bool fits = p + n <= c.cap;
+    for (u64 j = 0; j < n && p + j < c.cap; ++j)
+        st_rlx(c.map + p + j, fits ? (((u64)v << 32) | (j + 1)) : kSkipChunk);   // never 0 (0 = not written)
+    return fits;
+}
+
+// Warp: phase 1 -- dequeue until EMPTY, gather light vertices, publish heavy ones.
+template <int KIND>
+__device__ void level_dequeue(const gq_dev& cur, const gq_dev& nxt, const LevelCtx& c, u32* cnt, u64* edges) {
+    bool active = true;
+    for (u32 round = 0; round < kRetryLimit; ++round) {
+        unsigned int v = 0;
+        int s = GQ_EMPTY;
+        if (active) s = queue_dequeue<unsigned int, KIND>(cur, &v, c.rec);
+        active = active && (s == GQ_OK);   // an EMPTY is final within a level
+        if (!__ballot_sync(kFull, active)) break;
+        u64 b = 0, d = 0;
+        if (active) {
+            b = c.off[v];
+            d = c.off[v + 1] - b;
+            if (d >= kHeavyDeg && chunk_publish(c, v, d)) d = 0;
+        }
+        warp_gather<KIND>(nxt, c, b, d, cnt, edges);
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence();                    // the chunk words are written before `done` counts this warp
+        faa_rlx(c.done, 1);
+    }
+}
+
+// Warp: phase 2 -- take chunks until the level has none left.  Returns false
+// if a wait expired (the caller latches an error).
+template <int KIND>
+__device__ bool level_chunks(const gq_dev& nxt, const LevelCtx& c, u32* cnt, u64* edges) {
+    const u32 lane = threadIdx.x & 31;
+    const u64 t0 = globaltimer();
+    for (u32 polls = 0;; ++polls) {
+        // lane 0 decides: 0 = leave, 1 = chunk word in `item`, 2 = poll again, 3 = expired
+        u64 item = 0;
+        u32 what = 2;
+        if (lane == 0) {
+            const u64 fin = ld_acq(c.done);
+            u64 res = ld_acq(c.reserved);
+            if (res > c.cap) res = c.cap;
+            const u64 h = ld_rlx(c.handed);
+            if (h < res) {
+                const u64 g = faa_rlx(c.handed, 1);
+                if (g < c.cap) {
+                    // position g is (or will be) reserved unless the level closes first
+                    for (u32 w = 0;; ++w) {
+                        item = ld_acq(c.map + g);
+                        if (item) {
+                            st_rlx(c.map + g, 0);
+                            what = 1;
+                            break;
+                        }
+                        if (ld_acq(c.done) == c.dequeuers) {
+                            u64 r2 = ld_acq(c.reserved);
+                            if (g >= r2) {
+                                what = 0;
+                                break;
+                            }
+                            item = ld_acq(c.map + g);
+                            if (item) continue;
+                        }
+                        if (globaltimer() - t0 > kChunkWaitNs) {
+                            what = 3;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                } else {
+                    what = 0;
+                }
+            } else if (fin == c.dequeuers) {
+                what = 0;
+            } else if (globaltimer() - t0 > kChunkWaitNs) {
+                what = 3;
+            }
+        }
+        what = __shfl_sync(kFull, what, 0);
+        if (what == 0) return true;
+        if (what == 3) return false;
+        if (what == 2) {
+            __nanosleep(polls < 64 ? 64 : 256);
+            continue;
+        }
+        item = __shfl_sync(kFull, item, 0);
+        if (item == kSkipChunk) continue;
+        const u32 v = (u32)(item >> 32);
+        const u64 k = (item & 0xFFFFFFFFull) - 1;
+        const u64 vb = c.off[v], ve = c.off[v + 1];
+        const u64 b = vb + k * kChunk;
+        const u64 e = b + kChunk < ve ? b + kChunk : ve;
+        if (lane == 0) *edges += e - b;
+        for (u64 j = b + lane; j < e; j += 32) bfs_visit<KIND>(nxt, c.dist, c.adj[j], c.next_level, c.rec, cnt);
+        __syncwarp();
+    }
+}
+
+// One level-synchronous BFS by the threads of a thread-block cluster on the
+// frontier queues qa / qb (left empty).  ctl[0..2]: rotating frontier counts;
+// table: this cluster's chunk map of `cap` positions.  Returns the number of
+// levels; adds scanned edges to *edges; a chunk wait that expired is latched
+// in *err (nullable).
+template <int KIND>
+__device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* table, u64 cap,
+                           const gq_bfs_instance& g, u32* dist, u32 ct, u32 nct, cg::cluster_group& cluster,
+                           u64* edges, unsigned long long* err) {
+    const u32 cw = ct >> 5, nwarps = nct >> 5;
     for (u64 v = ct; v < g.n; v += nct) dist[v] = kUnreached;
     if (ct == 0) {
         st_rlx(ctl + 0, 0);
         st_rlx(ctl + 1, 0);
         st_rlx(ctl + 2, 0);
+        for (u32 w = 0; w < 9; ++w) st_rlx(table + w, 0);
     }
     cluster.sync();
     if (ct == 0) {
@@ -64,39 +273,19 @@ __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, const g
     for (;; ++level) {
         const u64 frontier = ld_acq(ctl + level % 3);
         if (frontier == 0) break;
-        if (ct == 0) st_rlx(ctl + (level + 2) % 3, 0);
+        if (ct == 0) {
+            st_rlx(ctl + (level + 2) % 3, 0);
+            chunk_prepare_next(table, level);
+        }
+        const u64 want = (frontier + 31) / 32;
+        const u64 dq = want < nwarps ? want : nwarps;
+        const LevelCtx c = level_ctx(reinterpret_cast<const u64*>(g.d_offsets), g.d_adj, dist, level, ct, table, cap,
+                                     dq);
         const gq_dev& cur = (level & 1) ? qb : qa;
         const gq_dev& nxt = (level & 1) ? qa : qb;
         u32 cnt = 0;
-        if (cw < (frontier + 31) / 32 || cw < 1) {
-            bool active = true;
-            for (u32 round = 0; round < kRetryLimit; ++round) {
-                unsigned int v = 0;
-                int s = GQ_EMPTY;
-                if (active) s = queue_dequeue<unsigned int, KIND>(cur, &v, ct);
-                active = active && (s == GQ_OK);
-                if (!__ballot_sync(0xffffffffu, active)) break;
-                u64 b = 0, e = 0;
-                if (active) {
-                    b = g.d_offsets[v];
-                    e = g.d_offsets[v + 1];
-                    if (e - b < 32) {
-                        *edges += e - b;
-                        for (u64 k = b; k < e; ++k) bfs_visit<KIND>(nxt, dist, g.d_adj[k], level + 1, ct, &cnt);
-                    }
-                }
-                u32 big = __ballot_sync(0xffffffffu, active && (e - b >= 32));
-                while (big) {
-                    const u32 owner = __ffs(big) - 1;
-                    big &= big - 1;
-                    const u64 bb = __shfl_sync(0xffffffffu, b, owner);
-                    const u64 ee = __shfl_sync(0xffffffffu, e, owner);
-                    if (lane == 0) *edges += ee - bb;
-                    for (u64 k = bb + lane; k < ee; k += 32) bfs_visit<KIND>(nxt, dist, g.d_adj[k], level + 1, ct, &cnt);
-                    __syncwarp();
-                }
-            }
-        }
+        if (cw < dq) level_dequeue<KIND>(cur, nxt, c, &cnt, edges);
+        if (!level_chunks<KIND>(nxt, c, &cnt, edges) && (threadIdx.x & 31) == 0 && err) atomicCAS(err, 0ull, 1ull);
         warp_add_full(reinterpret_cast<unsigned long long*>(ctl + (level + 1) % 3), cnt);
         cluster.sync();
     }

@@ -39,6 +39,8 @@ struct gq_queue {
     int device;
     int sm_count;
     uint64_t start_ticket;
+    void* aux;            // library-owned device scratch of the applications (gq_bfs), made on first use
+    uint64_t aux_bytes;
 };
 
 // Status helpers

@@ -69,14 +69,15 @@ __device__ __forceinline__ void thr_reset(i64* thr, i64 v, unsigned int* err) {
 }
 __device__ __forceinline__ i64 thr_dec(i64* thr) { return aref<i64>(*thr).fetch_add(-1, kRlx); }
 
-// Catch Tail up to at least `head` (Algorithm 1 TryDeq, "catch up Tail").
-__device__ __forceinline__ void ring_catchup(const gq_ring_view& r, u64 tail, u64 head) {
-    for (u32 it = 0; it < kRetryLimit; ++it) {
-        if (cas(r.tail, tail, head)) return;
-        head = ld_rlx(r.head);
-        tail = ld_rlx(r.tail);
-        if ((i64)(tail - head) >= 0) return;
-    }
+// Catch Tail up to at least `head` = this dequeuer's ticket + 1 (Algorithm 1
+// TryDeq, "catch up Tail").  One atomic maximum: Tail only grows, by fetch-add
+// (enqueuers) or by this maximum, and afterwards Tail >= head, which is all an
+// EMPTY dequeue needs so that later enqueuers take tickets past it.  A CAS loop
+// that re-reads Head instead chases every concurrent dequeuer's ticket, and
+// with tens of thousands of lanes turning EMPTY together it ran for
+// milliseconds.
+__device__ __forceinline__ void ring_catchup(const gq_ring_view& r, u64 head) {
+    atomicMax(reinterpret_cast<unsigned long long*>(r.tail), head);
 }
 
 // Inner-ring enqueue of index `idx` (TryEnq of Algorithm 1, retried until it
@@ -140,7 +141,7 @@ __device__ int lfq_ring_deq(const gq_dev& q, const gq_ring_view& r, u32* idx) {
         }
         const u64 tl = ld_rlx(r.tail);
         if ((i64)(tl - (h + 1)) <= 0) {
-            ring_catchup(r, tl, h + 1);
+            ring_catchup(r, h + 1);
             thr_dec(r.threshold);
             return GQ_EMPTY;
         }

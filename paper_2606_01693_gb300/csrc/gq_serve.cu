@@ -66,6 +66,7 @@ struct ServeK {
     u64 nreq;
     u64* claim;                  // next ticket (device memory)
     u64* ctl;                    // 8 words per slot (device memory)
+    u64* tables;                 // chunk map per slot (device memory)
     unsigned long long* stats;   // edges scanned, requests served, first error (1 = wait limit, 2 = bad request)
     u64 wait_ns;
 };
@@ -128,7 +129,9 @@ __global__ void __launch_bounds__(256) k_serve(const gq_dev* __restrict__ fq, co
         if (t == kNoTicket) break;
         gq_bfs_instance g = a.graphs[(u32)gs];
         g.src = (u32)(gs >> 32);
-        const u32 levels = cluster_bfs<KIND>(qa, qb, ctl + 1, g, dist, ct, nct, cluster, &edges);
+        u64* table = a.tables + slot * (chunk_map_bytes(kClusterChunkCap) / 8);
+        const u32 levels = cluster_bfs<KIND>(qa, qb, ctl + 1, table, kClusterChunkCap, g, dist, ct, nct, cluster,
+                                             &edges, a.stats + 2);
         if (ct == 0) {
             ServeEntry* e = a.ring + (t & a.ring_mask);
             __threadfence_system();
@@ -334,8 +337,9 @@ int serve_persistent(Runtime& rt, Buffers& b, u64 nmax) {
     void* d_mapped = nullptr;
     if (cudaHostGetDevicePointer(&d_mapped, b.mapped, 0) != cudaSuccess) return GQ_ERR_CUDA;
 
-    // device block: claim (256 B) | ctl 64 B per slot | stats | views | graphs
-    const u64 o_ctl = 256, o_stats = round256(o_ctl + 64ull * slots), o_views = o_stats + 256,
+    // device block: claim (256 B) | ctl 64 B per slot | stats | chunk maps | views | graphs
+    const u64 o_ctl = 256, o_stats = round256(o_ctl + 64ull * slots), o_tables = o_stats + 256,
+              o_views = round256(o_tables + slots * chunk_map_bytes(kClusterChunkCap)),
               o_graphs = round256(o_views + 2ull * slots * sizeof(gq_dev)),
               total = round256(o_graphs + (u64)c.ngraphs * sizeof(gq_bfs_instance));
     if (cudaMalloc(&b.dev, total) != cudaSuccess) return GQ_ERR_NOMEM;
@@ -360,6 +364,7 @@ int serve_persistent(Runtime& rt, Buffers& b, u64 nmax) {
     a.claim = reinterpret_cast<u64*>(d);
     a.ctl = reinterpret_cast<u64*>(d + o_ctl);
     a.stats = reinterpret_cast<unsigned long long*>(d + o_stats);
+    a.tables = reinterpret_cast<u64*>(d + o_tables);
     const double limit = c.wait_limit_s > 0 ? c.wait_limit_s : 30.0;
     a.wait_ns = (u64)(limit * 1e9);
     const gq_dev* dv = reinterpret_cast<const gq_dev*>(d + o_views);
