@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, 
     const u32 warp = tid >> 5, nwarps = nthreads >> 5;
     for (u64 v = tid; v < n; v += nthreads) dist[v] = kUnreached;
     if (tid == 0)
-        for (u32 w = 0; w < 9; ++w) st_rlx(table + w, 0);
+        for (u32 w = 0; w < 12; ++w) st_rlx(table + w, 0);
     if (!grid_barrier(ctl, gridDim.x)) return;
     if (tid == 0) {
         dist[src] = 0;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, 
         }
         const u64 want = (frontier + 31) / 32;
         const u64 dq = want < nwarps ? want : nwarps;
-        const LevelCtx c = level_ctx(off, adj, dist, level, tid, table, cap, dq);
+        const LevelCtx c = level_ctx(off, adj, dist, level, tid, table, cap, frontier, dq);
         const gq_dev& cur = (level & 1) ? qb : qa;
         const gq_dev& nxt = (level & 1) ? qa : qb;
         u32 cnt = 0;

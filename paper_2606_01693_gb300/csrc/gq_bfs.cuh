@@ -71,7 +71,7 @@ constexpr u64 kChunkWaitNs = 4000000000ull;     // bound of any wait for a chunk
 constexpr u64 kClusterChunkCap = 1u << 14;      // chunk-map positions of one cluster's search
 
 // Map memory: 16 header words, per level rotating by 3: reserved [0..2],
-// handed [3..5], done [6..8]; then the map itself, cap words, all zero
+// handed [3..5], done [6..8], taken [9..11]; then the map itself, cap words, all zero
 // between levels (every written word is cleared by the warp that scans it).
 // A map word is (vertex << 32) | (chunk index + 1), or kSkipChunk.
 __host__ __device__ constexpr u64 chunk_map_bytes(u64 cap) { return (16 + cap) * sizeof(u64); }
@@ -86,11 +86,13 @@ struct LevelCtx {
     u64* reserved;
     u64* handed;
     u64* done;
+    u64* taken;             // dequeues reserved this level
+    u64 frontier;           // items in the current frontier queue
     u64 dequeuers;          // warps that dequeue this level
 };
 
 __device__ __forceinline__ LevelCtx level_ctx(const u64* off, const u32* adj, u32* dist, u32 level, u32 rec,
-                                              u64* table, u64 cap, u64 dequeuers) {
+                                              u64* table, u64 cap, u64 frontier, u64 dequeuers) {
     LevelCtx c;
     c.off = off;
     c.adj = adj;
@@ -102,6 +104,8 @@ __device__ __forceinline__ LevelCtx level_ctx(const u64* off, const u32* adj, u3
     c.reserved = table + level % 3;
     c.handed = table + 3 + level % 3;
     c.done = table + 6 + level % 3;
+    c.taken = table + 9 + level % 3;
+    c.frontier = frontier;
     c.dequeuers = dequeuers;
     return c;
 }
@@ -113,6 +117,7 @@ __device__ __forceinline__ void chunk_prepare_next(u64* table, u32 level) {
     st_rlx(table + r, 0);
     st_rlx(table + 3 + r, 0);
     st_rlx(table + 6 + r, 0);
+    st_rlx(table + 9 + r, 0);
 }
 
 // Warp: scans the adjacency lists [b, b + d) of its lanes as one combined list.
@@ -151,15 +156,26 @@ __device__ __forceinline__ bool chunk_publish(const LevelCtx& c, u32 v, u64 d) {
     return fits;
 }
 
-// Warp: phase 1 -- dequeue until EMPTY, gather light vertices, publish heavy ones.
+// Warp: phase 1 -- dequeue the frontier, gather light vertices, publish heavy
+// ones.  The level knows its frontier size F, so a lane first reserves one of
+// the F items (warp-aggregated fetch-add on `taken`) and only then dequeues:
+// every dequeue finds an item and none returns EMPTY.  (EMPTY dequeues would
+// cost a ticket each -- for G-WFQ-YMC a pool cell that the next level's
+// enqueuers would have to step over.)  A dequeue that fails anyway latches
+// GQ_ERR_INVALID in the queue.
 template <int KIND>
 __device__ void level_dequeue(const gq_dev& cur, const gq_dev& nxt, const LevelCtx& c, u32* cnt, u64* edges) {
     bool active = true;
     for (u32 round = 0; round < kRetryLimit; ++round) {
         unsigned int v = 0;
-        int s = GQ_EMPTY;
-        if (active) s = queue_dequeue<unsigned int, KIND>(cur, &v, c.rec);
-        active = active && (s == GQ_OK);   // an EMPTY is final within a level
+        if (active) active = warp_faa(c.taken, 1) < c.frontier;
+        if (active) {
+            const int s = queue_dequeue<unsigned int, KIND>(cur, &v, c.rec);
+            if (s != GQ_OK) {
+                if (s == GQ_EMPTY) latch_error(cur.err, GQ_ERR_INVALID);
+                active = false;
+            }
+        }
         if (!__ballot_sync(kFull, active)) break;
         u64 b = 0, d = 0;
         if (active) {
@@ -261,7 +277,7 @@ __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* ta
         st_rlx(ctl + 0, 0);
         st_rlx(ctl + 1, 0);
         st_rlx(ctl + 2, 0);
-        for (u32 w = 0; w < 9; ++w) st_rlx(table + w, 0);
+        for (u32 w = 0; w < 12; ++w) st_rlx(table + w, 0);
     }
     cluster.sync();
     if (ct == 0) {
@@ -280,7 +296,7 @@ __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* ta
         const u64 want = (frontier + 31) / 32;
         const u64 dq = want < nwarps ? want : nwarps;
         const LevelCtx c = level_ctx(reinterpret_cast<const u64*>(g.d_offsets), g.d_adj, dist, level, ct, table, cap,
-                                     dq);
+                                     frontier, dq);
         const gq_dev& cur = (level & 1) ? qb : qa;
         const gq_dev& nxt = (level & 1) ? qa : qb;
         u32 cnt = 0;
