@@ -71,7 +71,7 @@ gq_layout make_layout(int kind, uint64_t cap, uint32_t elem, uint32_t max_thread
     memset(&L, 0, sizeof(L));
     uint64_t off = 0;
     L.ctrl = off;
-    off += kCtlLines * kLine;
+    off += kCtlLines * kCtlStride;
     if (kind == GQ_YMC) {
         const uint64_t cells = cap + 1;  // tickets start at 1; cell index = ticket
         off = align_up(off, 256); L.cell_val = off; off += cells * 8;
@@ -333,22 +333,22 @@ extern "C" int gq_create(int kind, uint64_t capacity, uint32_t elem_bytes, uint3
         d.thr_reset = (int64_t)(3 * capacity) - 1;
     }
     void* b = h->ws;
-    d.err = at<unsigned int>(b, h->lay.ctrl + kCtlErr * kLine);
-    d.scratch = at<unsigned long long>(b, h->lay.ctrl + kCtlScratch * kLine);
+    d.err = at<unsigned int>(b, h->lay.ctrl + kCtlErr * kCtlStride);
+    d.scratch = at<unsigned long long>(b, h->lay.ctrl + kCtlScratch * kCtlStride);
     if (kind == GQ_YMC) {
-        d.ymc_tail = at<unsigned long long>(b, h->lay.ctrl + kCtlYmcTail * kLine);
-        d.ymc_head = at<unsigned long long>(b, h->lay.ctrl + kCtlYmcHead * kLine);
+        d.ymc_tail = at<unsigned long long>(b, h->lay.ctrl + kCtlYmcTail * kCtlStride);
+        d.ymc_head = at<unsigned long long>(b, h->lay.ctrl + kCtlYmcHead * kCtlStride);
         d.cell_val = at<unsigned long long>(b, h->lay.cell_val);
         d.cell_enq = at<unsigned long long>(b, h->lay.cell_enq);
         d.cell_deq = at<unsigned long long>(b, h->lay.cell_deq);
         d.ymc_rec = at<unsigned long long>(b, h->lay.ymc_rec);
     } else {
-        d.aq.head = at<unsigned long long>(b, h->lay.ctrl + kCtlAqHead * kLine);
-        d.aq.tail = at<unsigned long long>(b, h->lay.ctrl + kCtlAqTail * kLine);
-        d.aq.threshold = at<long long>(b, h->lay.ctrl + kCtlAqThr * kLine);
-        d.fq.head = at<unsigned long long>(b, h->lay.ctrl + kCtlFqHead * kLine);
-        d.fq.tail = at<unsigned long long>(b, h->lay.ctrl + kCtlFqTail * kLine);
-        d.fq.threshold = at<long long>(b, h->lay.ctrl + kCtlFqThr * kLine);
+        d.aq.head = at<unsigned long long>(b, h->lay.ctrl + kCtlAqHead * kCtlStride);
+        d.aq.tail = at<unsigned long long>(b, h->lay.ctrl + kCtlAqTail * kCtlStride);
+        d.aq.threshold = at<long long>(b, h->lay.ctrl + kCtlAqThr * kCtlStride);
+        d.fq.head = at<unsigned long long>(b, h->lay.ctrl + kCtlFqHead * kCtlStride);
+        d.fq.tail = at<unsigned long long>(b, h->lay.ctrl + kCtlFqTail * kCtlStride);
+        d.fq.threshold = at<long long>(b, h->lay.ctrl + kCtlFqThr * kCtlStride);
         d.aq.slots = at<unsigned long long>(b, h->lay.aq_slots);
         d.fq.slots = at<unsigned long long>(b, h->lay.fq_slots);
         d.data = at<void>(b, h->lay.data);

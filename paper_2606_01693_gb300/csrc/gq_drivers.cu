@@ -59,21 +59,42 @@ __global__ void __launch_bounds__(256, 4) k_run(const __grid_constant__ gq_dev q
             if (a.delay_ns) __nanosleep(mix32(t, i) % a.delay_ns);
             const u64 tc = a.call ? globaltimer() : 0;
             int s;
-            u64 v;
-            if (is_enq) {
-                v = (sizeof(T) == 4) ? (((u64)t << 16) | seq) : (((u64)t << 32) | (u64)(seq + 1));
-                ++seq;
-                s = queue_enqueue<T, KIND>(q, (T)v, t);
-                if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
-                else if (s == GQ_FULL) ++c_full;
-                else ++c_err;
+            u64 v = 0;
+            if constexpr (KIND == GQ_YMC) {
+                // two operations with little in common: separate branches
+                if (is_enq) {
+                    v = (sizeof(T) == 4) ? (((u64)t << 16) | seq) : (((u64)t << 32) | (u64)(seq + 1));
+                    ++seq;
+                    s = queue_enqueue<T, KIND>(q, (T)v, t);
+                    if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
+                    else if (s == GQ_FULL) ++c_full;
+                    else ++c_err;
+                } else {
+                    T x = 0;
+                    s = queue_dequeue<T, KIND>(q, &x, t);
+                    v = (s == GQ_OK) ? (u64)x : 0;
+                    if (s == GQ_OK) { ++c_deq_ok; s_deq += v; }
+                    else if (s == GQ_EMPTY) ++c_empty;
+                    else ++c_err;
+                }
             } else {
-                T x = 0;
-                s = queue_dequeue<T, KIND>(q, &x, t);
-                v = (s == GQ_OK) ? (u64)x : 0;
-                if (s == GQ_OK) { ++c_deq_ok; s_deq += v; }
-                else if (s == GQ_EMPTY) ++c_empty;
-                else ++c_err;
+                // mirrored operations: enqueue and dequeue lanes run together
+                if (is_enq) {
+                    v = (sizeof(T) == 4) ? (((u64)t << 16) | seq) : (((u64)t << 32) | (u64)(seq + 1));
+                    ++seq;
+                }
+                T x = (T)v;
+                s = queue_op<T, KIND>(q, is_enq, &x, t);
+                if (is_enq) {
+                    if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
+                    else if (s == GQ_FULL) ++c_full;
+                    else ++c_err;
+                } else {
+                    v = (s == GQ_OK) ? (u64)x : 0;
+                    if (s == GQ_OK) { ++c_deq_ok; s_deq += v; }
+                    else if (s == GQ_EMPTY) ++c_empty;
+                    else ++c_err;
+                }
             }
             const u64 j = (u64)i * a.threads + t;
             if (a.end) a.end[j] = globaltimer();

@@ -192,4 +192,28 @@ __device__ int lfq_dequeue(const gq_dev& q, T* v) {
     return s == GQ_OK ? GQ_OK : s;
 }
 
+// Enqueue (enq = true, payload *v) or dequeue (enq = false, result in *v) on
+// one code path.  Both are "take an index from one ring, move the payload,
+// give the index to the other ring": enqueue takes from fq and gives to aq,
+// dequeue the reverse.  Selecting the rings per lane lets a warp whose lanes
+// mix enqueues and dequeues run them together instead of one after the other
+// (divergent branches); WaveFAA groups the lanes by counter address.  Each
+// lane performs exactly the steps of its own operation.
+template <class T>
+__device__ int lfq_op(const gq_dev& q, bool enq, T* v) {
+    const gq_ring_view& from = enq ? q.fq : q.aq;
+    const gq_ring_view& to = enq ? q.aq : q.fq;
+    u32 i;
+    int s = lfq_ring_deq<true>(q, from, &i);
+    if (s == GQ_EMPTY) return enq ? GQ_FULL : GQ_EMPTY;
+    if (s != GQ_OK) return s;
+    if (i >= q.capacity) {                            // never expected: a corrupt ring entry
+        latch_error(q.err, GQ_ERR_INVALID);
+        return GQ_ERR_INVALID;
+    }
+    if (enq) data_store<T>(q, i, *v);                 // ordered before the release CAS in aq
+    else *v = data_load<T>(q, i);                     // after the acquire on the aq slot
+    return lfq_ring_enq<true>(q, to, i);
+}
+
 }  // namespace gqd

@@ -25,4 +25,14 @@ __device__ __forceinline__ int queue_dequeue(const gq_dev& q, T* v, u32 tid) {
     else return ymc_dequeue<T, MATCH>(q, v, tid);
 }
 
+// Enqueue (enq, payload *v) or dequeue (!enq, result in *v) chosen per lane.
+// G-LFQ and G-WFQ run both on one code path (their operations mirror each
+// other over the two index rings); G-WFQ-YMC branches.
+template <class T, int KIND>
+__device__ __forceinline__ int queue_op(const gq_dev& q, bool enq, T* v, u32 tid) {
+    if constexpr (KIND == GQ_LFQ) return lfq_op<T>(q, enq, v);
+    else if constexpr (KIND == GQ_WFQ) return wfq_op<T>(q, enq, v, tid);
+    else return enq ? ymc_enqueue<T, false>(q, *v, tid) : ymc_dequeue<T, false>(q, v, tid);
+}
+
 }  // namespace gqd

@@ -546,4 +546,27 @@ __device__ int wfq_dequeue(const gq_dev& q, T* v, u32 tid) {
     return s == GQ_OK ? GQ_OK : s;
 }
 
+// Enqueue or dequeue on one code path (see lfq_op): the rings are chosen per
+// lane, so mixed warps run both kinds of operation together.
+template <class T>
+__device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid) {
+    if (tid >= q.max_threads) {
+        latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
+        return GQ_ERR_TOO_MANY_THREADS;
+    }
+    const gq_ring_view& from = enq ? q.fq : q.aq;
+    const gq_ring_view& to = enq ? q.aq : q.fq;
+    u32 i;
+    int s = wfq_ring_deq<true>(from, q, &i, tid, q.patience_deq);
+    if (s == GQ_EMPTY) return enq ? GQ_FULL : GQ_EMPTY;
+    if (s != GQ_OK) return s;
+    if (i >= q.capacity) {
+        latch_error(q.err, GQ_ERR_INVALID);
+        return GQ_ERR_INVALID;
+    }
+    if (enq) data_store<T>(q, i, *v);
+    else *v = data_load<T>(q, i);
+    return wfq_ring_enq<true>(to, q, i, tid, q.patience_enq);
+}
+
 }  // namespace gqd
