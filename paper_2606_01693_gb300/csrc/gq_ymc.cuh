@@ -50,7 +50,8 @@ namespace gqd {
 constexpr u64 kVBot = ~0ull;
 constexpr u64 kVTop = ~0ull - 1;
 constexpr u64 kRefBot = 0, kRefTop = 1;
-constexpr u32 kYSpin = 16;      // reads of an empty cell before marking it unusable
+constexpr u32 kYSpin = 16;      // back-to-back reads of an empty cell (its enqueuer may be on its way)
+constexpr u32 kYWaitPolls = 256; // then, if T shows the ticket taken, polls 64 ns apart
 
 enum : int {
     kYErId = 0,    // enqueue request: > 0 pending from cell id on, < 0 done at cell -id
@@ -94,6 +95,17 @@ static __device__ __noinline__ int ymc_help_enq(const gq_dev& q, u32 me, u64 i, 
     u64* ce = q.cell_enq + i;
     u64 x = ld_acq(cv);
     for (u32 s = 0; s < kYSpin && x == kVBot; ++s) x = ld_acq(cv);   // an enqueuer may be on its way
+    if (x == kVBot && ld_acq(q.ymc_tail) > i) {
+        // T > i: the enqueuer holding ticket i has taken it and its write is
+        // due.  Marking the cell unusable now would send that enqueuer round
+        // again, and under load such retries feed on themselves (H runs ahead
+        // of T, more cells are found empty, more enqueuers retry).  Wait
+        // longer for the write, boundedly.
+        for (u32 s = 0; s < kYWaitPolls && x == kVBot; ++s) {
+            __nanosleep(64);
+            x = ld_acq(cv);
+        }
+    }
     if (x == kVBot) {
         if (!cas(cv, x, kVTop) && x != kVTop) { *v = x; return kYValue; }
         x = kVTop;
