@@ -38,7 +38,11 @@ METRIC = "queue Mops/s (enq+deq) vs threads; % of measured L2-atomic peak; servi
 CAPACITY = 1 << 20
 # DRAM bytes per launch of each run kernel from one ncu capture (profiles/);
 # None until captured for the current kernels.
-NCU_TRAFFIC = {"lfq": None, "wfq": None, "ymc": None}
+# DRAM bytes (read + write) per launch of each run kernel at the headline size, from one ncu
+# capture of `bench.py --steps 1 --warmup 3 --no-sweep --no-e2e --no-cpu --no-apps --no-batched
+# --no-serving` with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass; profiles/).
+# Set to None whenever the kernels change.
+NCU_TRAFFIC = {"lfq": 46699776 + 13850368, "wfq": 63783680 + 206591232, "ymc": 986322176 + 827432960}
 
 
 def parse():
@@ -57,6 +61,7 @@ def parse():
     p.add_argument("--cpu-threads", type=int, default=1 << 17, help="logical threads in the CPU sample")
     p.add_argument("--no-apps", action="store_true", help="skip the application measurements (BFS, ray tracing)")
     p.add_argument("--no-batched", action="store_true", help="skip the batched / persistent / graph comparisons")
+    p.add_argument("--no-serving", action="store_true", help="skip the BFS serving measurements")
     return p.parse_args()
 
 
@@ -296,6 +301,34 @@ def bench_batched(gq, synth, kinds, dev, reps=3):
     return out
 
 
+def bench_serving(gq, synth, kinds, dev, pool_graphs=64, seed=2026):
+    """BFS serving: a resident pool of R-MAT graphs (scale uniform in 10..20 by
+    seed, i.e. log-uniform vertex counts), requests (graph, source) with Poisson
+    arrivals at 100..10,000 req/s, admission against a 32 GiB budget.  Persistent
+    device scheduler (clusters of 8 blocks fed by the mapped request ring) vs one
+    gq_bfs launch per request.  Latency = host-observed completion - arrival."""
+    import torch
+    scales = synth.rmat_pool_scales(pool_graphs, 10, 20, seed)
+    host = [synth.rmat_csr_fast(int(sc), seed=seed * 1000 + i) for i, sc in enumerate(scales)]
+    devg = [(torch.from_numpy(o.view(np.int64)).to(dev), torch.from_numpy(a.view(np.int32)).to(dev)) for o, a in host]
+    offs = [h[0] for h in host]
+    out = {"pool": {"graphs": pool_graphs, "scales": "uniform 10..20", "edges": int(sum(len(a) for _, a in host)),
+                    "budget_gib": 32}}
+    for rate in (100, 300, 1000, 3000, 10000):
+        nreq = int(min(2000, max(200, rate)))
+        gid, src, arr = synth.serving_requests(offs, nreq, float(rate), seed + rate)
+        for k in kinds:
+            for mode in ("persistent", "per_request"):
+                r = gq.gq_serve(k, devg, gid, src, arr, mode=mode, cluster_blocks=8, budget_bytes=32 << 30)
+                lat = r["latency_s"] * 1e3
+                out["%s_%s_%d" % (k, mode, rate)] = {
+                    "requests": nreq, "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                    "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                    "throughput_rps": round(nreq / r["wall_s"], 1), "admission_waits": int(r["admission_waits"]),
+                    "peak_state_gib": round(r["peak_state_bytes"] / 2**30, 3), "slots": int(r["slots_used"])}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -367,14 +400,16 @@ def main():
         e1.record()
         e1.synchronize()
         ops = blocks * threads * iters
-        if pattern == gq.GQ_PEAK_SAME_ADDR_FAA:
+        if pattern in (gq.GQ_PEAK_SAME_ADDR_FAA, gq.GQ_PEAK_SPREAD_FAA, gq.GQ_PEAK_PACKED_FAA):
             ops //= 32
         return ops / (e0.elapsed_time(e1) * 1e-3) / 1e9
 
     peaks = {"same_addr_faa_gops": time_peak(gq.GQ_PEAK_SAME_ADDR_FAA, 64),
              "coalesced_cas_gops": time_peak(gq.GQ_PEAK_COALESCED_CAS, 64),
              "scattered_cas_gops": time_peak(gq.GQ_PEAK_SCATTERED_CAS, 64),
-             "coalesced_load_gops": time_peak(gq.GQ_PEAK_COALESCED_LOAD, 64)}
+             "coalesced_load_gops": time_peak(gq.GQ_PEAK_COALESCED_LOAD, 64),
+             "faa_16_counters_4k_apart_gops": time_peak(gq.GQ_PEAK_SPREAD_FAA, 64),
+             "faa_16_counters_128b_apart_gops": time_peak(gq.GQ_PEAK_PACKED_FAA, 64)}
 
     # ---- workload ----
     sched = synth.mixed_schedule_bits(args.seed, T, K)
@@ -541,6 +576,9 @@ def main():
     batched = None
     if not args.no_batched:
         batched = bench_batched(gq, synth, kinds, dev)
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = bench_serving(gq, synth, kinds, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -558,7 +596,7 @@ def main():
                            "l2": "flushed between timed steps (256 MiB write); queue state re-initialised inside "
                                  "each step"},
                 "roofline": roofline, "peaks": peaks, "per_queue": per_queue, "sweep": sweep,
-                "cpu_baseline": cpu, "e2e": e2e, "apps": apps, "batched": batched,
+                "cpu_baseline": cpu, "e2e": e2e, "apps": apps, "batched": batched, "serving": serving,
                 "gpu_launches": args.steps * sum(launches_per_step[k] for k in kinds),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -90,14 +90,19 @@ enum {
     GQ_PEAK_SAME_ADDR_FAA = 0,   /* one lane per warp, fetch-add on one shared word      */
     GQ_PEAK_COALESCED_CAS = 1,   /* each warp CASes 32 consecutive words (2 lines)       */
     GQ_PEAK_SCATTERED_CAS = 2,   /* each lane CASes a pseudo-random word                 */
-    GQ_PEAK_COALESCED_LOAD = 3   /* each warp loads 32 consecutive words (reference)     */
+    GQ_PEAK_COALESCED_LOAD = 3,  /* each warp loads 32 consecutive words (reference)     */
+    GQ_PEAK_SPREAD_FAA = 4,      /* one lane per warp, fetch-add on one of 16 counters    */
+                                 /* 4096 bytes apart (warp id mod 16)                    */
+    GQ_PEAK_PACKED_FAA = 5       /* the same on 16 counters 128 bytes apart              */
 };
 
 /* Runs `iters` rounds of the pattern on a grid of blocks x threads over the
  * caller's buffer d_buf[0..buf_words) (L2-resident when small enough).  Each
  * round is one atomic (or load) per participating lane.  d_sink receives a
  * value derived from the results so the work cannot be elided.
- * Time it with events on `stream`; ops = blocks * threads * iters (FAA: / 32). */
+ * Time it with events on `stream`; ops = blocks * threads * iters (FAA patterns: / 32).
+ * The two 16-counter patterns need buf_words >= 16 * 512 (SPREAD) or 16 * 16 (PACKED); they show
+ * whether hot counters at that spacing share an L2 slice (their rates do not add up if they do). */
 int gq_atomic_peak(int pattern, uint32_t blocks, uint32_t threads, uint32_t iters,
                    unsigned long long* d_buf, uint64_t buf_words, unsigned long long* d_sink,
                    void* stream);

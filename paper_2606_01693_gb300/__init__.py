@@ -28,6 +28,7 @@ GQ_ERR_INVALID, GQ_ERR_NOMEM, GQ_ERR_CUDA, GQ_ERR_TIMEOUT = -1, -2, -3, -4
 GQ_ERR_POOL_EXHAUSTED, GQ_ERR_TOO_MANY_THREADS, GQ_ERR_RESERVED_VALUE = -5, -6, -7
 GQ_RUN_PAIRS, GQ_RUN_MIXED, GQ_RUN_SPLIT = 0, 1, 2
 GQ_PEAK_SAME_ADDR_FAA, GQ_PEAK_COALESCED_CAS, GQ_PEAK_SCATTERED_CAS, GQ_PEAK_COALESCED_LOAD = 0, 1, 2, 3
+GQ_PEAK_SPREAD_FAA, GQ_PEAK_PACKED_FAA = 4, 5
 (GQ_CNT_ENQ_OK, GQ_CNT_ENQ_FULL, GQ_CNT_DEQ_OK, GQ_CNT_DEQ_EMPTY, GQ_CNT_SUM_ENQ, GQ_CNT_SUM_DEQ,
  GQ_CNT_ERRORS) = range(7)
 

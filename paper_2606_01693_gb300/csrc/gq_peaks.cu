@@ -6,7 +6,10 @@
 //   * same-address fetch-add: the ceiling of one hot ticket counter;
 //   * warp-coalesced CAS: 32 lanes on 32 consecutive 8-byte words, the access
 //     shape of a warp's slot CASes after WaveFAA handed it consecutive tickets;
-//   * scattered CAS: every lane on an unrelated word (no coalescing).
+//   * scattered CAS: every lane on an unrelated word (no coalescing);
+//   * fetch-add on 16 counters 4 KB apart and on 16 counters 128 B apart: a
+//     queue's hot counters only add up their single-address rates when they
+//     sit in different L2 slices, which decides the control-line spacing.
 #include <cuda_runtime.h>
 
 #include "../../include/gq_drivers.h"
@@ -52,6 +55,10 @@ __global__ void k_peak(int pattern, u32 iters, u64* buf, u64 words, unsigned lon
     if (pattern == GQ_PEAK_SAME_ADDR_FAA) {
         if (lane == 0)
             for (u32 i = 0; i < iters; ++i) acc += atom_add_relaxed(buf, 1);
+    } else if (pattern == GQ_PEAK_SPREAD_FAA || pattern == GQ_PEAK_PACKED_FAA) {
+        u64* c = buf + (warp % 16) * (pattern == GQ_PEAK_SPREAD_FAA ? 512 : 16);
+        if (lane == 0)
+            for (u32 i = 0; i < iters; ++i) acc += atom_add_relaxed(c, 1);
     } else if (pattern == GQ_PEAK_COALESCED_CAS) {
         for (u32 i = 0; i < iters; ++i) {
             const u64 g = hash64(warp * 0x9E3779B97F4A7C15ull + i) % groups;
@@ -76,8 +83,10 @@ __global__ void k_peak(int pattern, u32 iters, u64* buf, u64 words, unsigned lon
 extern "C" int gq_atomic_peak(int pattern, uint32_t blocks, uint32_t threads, uint32_t iters,
                               unsigned long long* d_buf, uint64_t buf_words, unsigned long long* d_sink,
                               void* stream) {
-    if (pattern < 0 || pattern > GQ_PEAK_COALESCED_LOAD || !d_buf || !d_sink) return GQ_ERR_INVALID;
+    if (pattern < 0 || pattern > GQ_PEAK_PACKED_FAA || !d_buf || !d_sink) return GQ_ERR_INVALID;
     if (blocks == 0 || threads == 0 || threads > 1024 || (threads & 31) || buf_words < 32) return GQ_ERR_INVALID;
+    if (pattern == GQ_PEAK_SPREAD_FAA && buf_words < 16 * 512) return GQ_ERR_INVALID;
+    if (pattern == GQ_PEAK_PACKED_FAA && buf_words < 16 * 16) return GQ_ERR_INVALID;
     k_peak<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(pattern, iters, d_buf, buf_words, d_sink);
     return gq_check_launch();
 }

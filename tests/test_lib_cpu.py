@@ -115,3 +115,13 @@ def test_serve_rejects_bad_config(change):
     assert gq.load().gq_serve(ctypes.byref(cfg), ctypes.byref(res)) == gq.GQ_ERR_INVALID
     assert gq.load().gq_serve(None, ctypes.byref(res)) == gq.GQ_ERR_INVALID
     assert gq.load().gq_serve(ctypes.byref(cfg), None) == gq.GQ_ERR_INVALID
+
+
+def test_atomic_peak_arguments_validated():
+    L = gq.load()
+    sink = ctypes.c_void_p(0x1000)   # never dereferenced: every call below fails validation first
+    buf = ctypes.c_void_p(0x2000)
+    assert L.gq_atomic_peak(6, 1, 32, 1, buf, 1 << 20, sink, None) == gq.GQ_ERR_INVALID
+    assert L.gq_atomic_peak(gq.GQ_PEAK_SPREAD_FAA, 1, 32, 1, buf, 16 * 512 - 1, sink, None) == gq.GQ_ERR_INVALID
+    assert L.gq_atomic_peak(gq.GQ_PEAK_PACKED_FAA, 1, 32, 1, buf, 16 * 16 - 1, sink, None) == gq.GQ_ERR_INVALID
+    assert L.gq_atomic_peak(gq.GQ_PEAK_SAME_ADDR_FAA, 1, 33, 1, buf, 64, sink, None) == gq.GQ_ERR_INVALID
