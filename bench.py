@@ -65,6 +65,20 @@ def parse():
     return p.parse_args()
 
 
+def replica_totals(total_ms, succ_ops, device=None):
+    """Replicas (one independent queue set per rank, no data exchange): the job's
+    time is the slowest rank's and its operations are the sum over ranks."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), float(succ_ops)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([float(succ_ops)], dtype=torch.float64, device=device)
+    dist.all_reduce(s)
+    return float(t.item()), float(s.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -463,17 +477,7 @@ def main():
     succ = {k: int(c[k][gq.GQ_CNT_ENQ_OK] + c[k][gq.GQ_CNT_DEQ_OK]) for k in kinds}
     for k in kinds:
         assert c[k][gq.GQ_CNT_ERRORS] == 0, k
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        s = torch.tensor([sum(succ.values())], dtype=torch.float64, device=dev)
-        dist.all_reduce(s)
-        all_succ = float(s.item())
-    else:
-        all_succ = float(sum(succ.values()))
+    total_ms, all_succ = replica_totals(float(sum(step_ms)), sum(succ.values()), dev)
     value = all_succ / (total_ms * 1e-3) / 1e6
 
     # ---- roofline of the dominant run kernel ----
