@@ -27,24 +27,28 @@ constexpr u32 kBarrierSpinLimit = 1u << 26;   // x ~100 ns sleeps: a few seconds
 constexpr u64 kGridChunkCap = 1u << 21;       // chunk-map positions of a whole-GPU search
 
 // Control words in the first queue's scratch line (words 8..15).
-enum { kCtlBarCount = 0, kCtlBarGen = 1, kCtlFront0 = 2, kCtlFront1 = 3, kCtlFront2 = 4, kCtlErr = 5 };
+enum { kCtlFront0 = 2, kCtlFront1 = 3, kCtlFront2 = 4, kCtlErr = 5 };
 
 // Device-wide barrier for a cooperative launch: the last block to arrive
 // resets the count and bumps the generation; the others wait for it, at most
-// kBarrierSpinLimit sleeps, after which they latch an error and go on.
-__device__ __forceinline__ bool grid_barrier(u64* ctl, u32 nblocks) {
+// kBarrierSpinLimit sleeps, after which they latch an error and go on.  The
+// count and the generation sit on different 4 KB lines of the search's table
+// (the arrivals' atomics do not queue behind the waiters' loads).
+__device__ __forceinline__ bool grid_barrier(u64* ctl, u64* table, u32 nblocks) {
     __shared__ int s_ok;
+    u64* count = table + kTabBarCount * kTabLine;
+    u64* generation = table + kTabBarGen * kTabLine;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const u64 gen = ld_acq(ctl + kCtlBarGen);
+        const u64 gen = ld_acq(generation);
         __threadfence();
-        if (atomicAdd(reinterpret_cast<unsigned long long*>(ctl + kCtlBarCount), 1ull) + 1 == nblocks) {
-            st_rlx(ctl + kCtlBarCount, 0);
-            st_rel(ctl + kCtlBarGen, gen + 1);
+        if (atomicAdd(reinterpret_cast<unsigned long long*>(count), 1ull) + 1 == nblocks) {
+            st_rlx(count, 0);
+            st_rel(generation, gen + 1);
         } else {
             u32 it = 0;
-            while (ld_acq(ctl + kCtlBarGen) == gen) {
+            while (ld_acq(generation) == gen) {
                 if (++it > kBarrierSpinLimit) {
                     atomicCAS(reinterpret_cast<unsigned long long*>(ctl + kCtlErr), 0ull, 1ull);
                     ok = 0;
@@ -70,13 +74,13 @@ __global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, 
     const u32 warp = tid >> 5, nwarps = nthreads >> 5;
     for (u64 v = tid; v < n; v += nthreads) dist[v] = kUnreached;
     if (tid == 0)
-        for (u32 w = 0; w < 12; ++w) st_rlx(table + w, 0);
-    if (!grid_barrier(ctl, gridDim.x)) return;
+        chunk_reset_all(table);
+    if (!grid_barrier(ctl, table, gridDim.x)) return;
     if (tid == 0) {
         dist[src] = 0;
         if (queue_enqueue<unsigned int, KIND>(qa, src, 0) == GQ_OK) st_rlx(ctl + kCtlFront0, 1);
     }
-    if (!grid_barrier(ctl, gridDim.x)) return;
+    if (!grid_barrier(ctl, table, gridDim.x)) return;
     u64 edges = 0, reached = 0;
     u32 level = 0;
     for (;; ++level) {
@@ -97,7 +101,7 @@ __global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, 
         if (!level_chunks<KIND>(nxt, c, &cnt, &edges) && (threadIdx.x & 31) == 0)
             atomicCAS(reinterpret_cast<unsigned long long*>(ctl + kCtlErr), 0ull, 2ull);
         warp_add_full(reinterpret_cast<unsigned long long*>(ctl + kCtlFront0 + (level + 1) % 3), cnt);
-        if (!grid_barrier(ctl, gridDim.x)) return;
+        if (!grid_barrier(ctl, table, gridDim.x)) return;
     }
     if (stats) warp_add_full(stats + 2, edges);
     if (tid == 0 && stats) {
@@ -133,6 +137,8 @@ int launch_bfs(gq_handle ha, gq_handle hb, uint64_t n, const uint64_t* off, cons
         ha->aux_bytes = bytes;
     }
     u64* table = static_cast<u64*>(ha->aux);
+    // a search that ended on an expired barrier wait may have left the count behind
+    if (cudaMemsetAsync(table + kTabBarCount * kTabLine, 0, sizeof(u64), st) != cudaSuccess) return GQ_ERR_CUDA;
     gq_dev qa = ha->dev, qb = hb->dev;
     const u64* o = reinterpret_cast<const u64*>(off);
     const u32* a = reinterpret_cast<const u32*>(adj);

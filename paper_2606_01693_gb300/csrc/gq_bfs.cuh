@@ -70,11 +70,23 @@ constexpr u64 kSkipChunk = ~0ull;
 constexpr u64 kChunkWaitNs = 4000000000ull;     // bound of any wait for a chunk word (4 s)
 constexpr u64 kClusterChunkCap = 1u << 14;      // chunk-map positions of one cluster's search
 
-// Map memory: 16 header words, per level rotating by 3: reserved [0..2],
-// handed [3..5], done [6..8], taken [9..11]; then the map itself, cap words, all zero
-// between levels (every written word is cleared by the warp that scans it).
+// Table memory: a header of six 4 KB lines, then the map itself (cap words, all
+// zero between levels: every written word is cleared by the warp that scans
+// it).  Header lines (three words each, rotating by level): reserved, handed,
+// done, taken; line 4 and 5 hold the whole-GPU search's barrier count and
+// generation.  Hot words on different 4 KB lines land in different L2 slices,
+// so the pollers of one word do not queue in front of the atomics on another.
 // A map word is (vertex << 32) | (chunk index + 1), or kSkipChunk.
-__host__ __device__ constexpr u64 chunk_map_bytes(u64 cap) { return (16 + cap) * sizeof(u64); }
+constexpr u64 kTabLine = 512;                   // words per header line (4 KB)
+constexpr u64 kTabHeader = 6 * kTabLine;
+enum { kTabReserved = 0, kTabHanded = 1, kTabDone = 2, kTabTaken = 3, kTabBarCount = 4, kTabBarGen = 5 };
+__host__ __device__ constexpr u64 chunk_map_bytes(u64 cap) { return (kTabHeader + cap) * sizeof(u64); }
+
+// Called by one thread before a search: clears the per-level counters.
+__device__ __forceinline__ void chunk_reset_all(u64* table) {
+    for (u32 l = 0; l < 4; ++l)
+        for (u32 r = 0; r < 3; ++r) st_rlx(table + l * kTabLine + r, 0);
+}
 
 struct LevelCtx {
     const u64* off;
@@ -99,12 +111,12 @@ __device__ __forceinline__ LevelCtx level_ctx(const u64* off, const u32* adj, u3
     c.dist = dist;
     c.next_level = level + 1;
     c.rec = rec;
-    c.map = table + 16;
+    c.map = table + kTabHeader;
     c.cap = cap;
-    c.reserved = table + level % 3;
-    c.handed = table + 3 + level % 3;
-    c.done = table + 6 + level % 3;
-    c.taken = table + 9 + level % 3;
+    c.reserved = table + kTabReserved * kTabLine + level % 3;
+    c.handed = table + kTabHanded * kTabLine + level % 3;
+    c.done = table + kTabDone * kTabLine + level % 3;
+    c.taken = table + kTabTaken * kTabLine + level % 3;
     c.frontier = frontier;
     c.dequeuers = dequeuers;
     return c;
@@ -114,10 +126,28 @@ __device__ __forceinline__ LevelCtx level_ctx(const u64* off, const u32* adj, u3
 // (last used during level L - 2).
 __device__ __forceinline__ void chunk_prepare_next(u64* table, u32 level) {
     const u32 r = (level + 1) % 3;
-    st_rlx(table + r, 0);
-    st_rlx(table + 3 + r, 0);
-    st_rlx(table + 6 + r, 0);
-    st_rlx(table + 9 + r, 0);
+    for (u32 l = 0; l < 4; ++l) st_rlx(table + l * kTabLine + r, 0);
+}
+
+// Lane: visits up to kVisitBatch edges at once.  The adjacency loads of the
+// batch are issued together, then the distance loads, so a lane has several
+// memory requests in flight instead of one dependent chain per edge.
+constexpr int kVisitBatch = 4;
+
+template <int KIND>
+__device__ __forceinline__ void visit_batch(const gq_dev& nxt, const LevelCtx& c, const u64 (&e)[kVisitBatch],
+                                            const bool (&ok)[kVisitBatch], u32* cnt) {
+    u32 w[kVisitBatch], d[kVisitBatch];
+#pragma unroll
+    for (int u = 0; u < kVisitBatch; ++u) w[u] = ok[u] ? __ldg(c.adj + e[u]) : 0u;
+#pragma unroll
+    for (int u = 0; u < kVisitBatch; ++u) d[u] = ok[u] ? aref<u32>(c.dist[w[u]]).load(kRlx) : 0u;
+#pragma unroll
+    for (int u = 0; u < kVisitBatch; ++u) {
+        if (!ok[u] || d[u] != kUnreached) continue;
+        if (atomicCAS(c.dist + w[u], kUnreached, c.next_level) != kUnreached) continue;
+        if (queue_enqueue<unsigned int, KIND>(nxt, w[u], c.rec) == GQ_OK) ++*cnt;
+    }
 }
 
 // Warp: scans the adjacency lists [b, b + d) of its lanes as one combined list.
@@ -133,15 +163,21 @@ __device__ void warp_gather(const gq_dev& nxt, const LevelCtx& c, u64 b, u64 d, 
     if (total == 0) return;
     if (lane == 0) *edges += total;
     const u64 start = b - (incl - d);   // combined index x of this lane's list is edge start + x (mod 2^64)
-    for (u64 base = 0; base < total; base += 32) {
-        const u64 x = base + lane;
-        u32 pos = 0;                     // first lane whose inclusive sum exceeds x
-        for (u32 step = 16; step; step >>= 1) {
-            const u64 v = __shfl_sync(kFull, incl, pos + step - 1);
-            if (v <= x) pos += step;
+    for (u64 base = 0; base < total; base += 32 * kVisitBatch) {
+        u64 e[kVisitBatch];
+        bool ok[kVisitBatch];
+#pragma unroll
+        for (int u = 0; u < kVisitBatch; ++u) {
+            const u64 x = base + 32 * u + lane;
+            u32 pos = 0;                 // first lane whose inclusive sum exceeds x
+            for (u32 step = 16; step; step >>= 1) {
+                const u64 v = __shfl_sync(kFull, incl, pos + step - 1);
+                if (v <= x) pos += step;
+            }
+            e[u] = __shfl_sync(kFull, start, pos) + x;
+            ok[u] = x < total;
         }
-        const u64 st = __shfl_sync(kFull, start, pos);
-        if (x < total) bfs_visit<KIND>(nxt, c.dist, c.adj[st + x], c.next_level, c.rec, cnt);
+        visit_batch<KIND>(nxt, c, e, ok, cnt);
     }
 }
 
@@ -257,7 +293,16 @@ __device__ bool level_chunks(const gq_dev& nxt, const LevelCtx& c, u32* cnt, u64
         const u64 b = vb + k * kChunk;
         const u64 e = b + kChunk < ve ? b + kChunk : ve;
         if (lane == 0) *edges += e - b;
-        for (u64 j = b + lane; j < e; j += 32) bfs_visit<KIND>(nxt, c.dist, c.adj[j], c.next_level, c.rec, cnt);
+        for (u64 j = b + lane; j < e; j += 32 * kVisitBatch) {
+            u64 ex[kVisitBatch];
+            bool ok[kVisitBatch];
+#pragma unroll
+            for (int u = 0; u < kVisitBatch; ++u) {
+                ex[u] = j + 32 * u;
+                ok[u] = ex[u] < e;
+            }
+            visit_batch<KIND>(nxt, c, ex, ok, cnt);
+        }
         __syncwarp();
     }
 }
@@ -277,7 +322,7 @@ __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* ta
         st_rlx(ctl + 0, 0);
         st_rlx(ctl + 1, 0);
         st_rlx(ctl + 2, 0);
-        for (u32 w = 0; w < 12; ++w) st_rlx(table + w, 0);
+        chunk_reset_all(table);
     }
     cluster.sync();
     if (ct == 0) {
