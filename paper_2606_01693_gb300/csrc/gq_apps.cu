@@ -34,8 +34,12 @@ enum { kCtlFront0 = 2, kCtlFront1 = 3, kCtlFront2 = 4, kCtlErr = 5 };
 // kBarrierSpinLimit sleeps, after which they latch an error and go on.  The
 // count and the generation sit on different 4 KB lines of the search's table
 // (the arrivals' atomics do not queue behind the waiters' loads).
-__device__ __forceinline__ bool grid_barrier(u64* ctl, u64* table, u32 nblocks) {
+// If `word` is given, thread 0 reads it after the barrier and every thread of
+// the block gets the value in *value (one load per block instead of per thread).
+__device__ __forceinline__ bool grid_barrier(u64* ctl, u64* table, u32 nblocks, u64* word = nullptr,
+                                             u64* value = nullptr) {
     __shared__ int s_ok;
+    __shared__ u64 s_val;
     u64* count = table + kTabBarCount * kTabLine;
     u64* generation = table + kTabBarGen * kTabLine;
     __syncthreads();
@@ -59,8 +63,10 @@ __device__ __forceinline__ bool grid_barrier(u64* ctl, u64* table, u32 nblocks) 
         }
         __threadfence();
         s_ok = ok && ld_acq(ctl + kCtlErr) == 0;
+        if (word) s_val = ld_acq(word);
     }
     __syncthreads();
+    if (word) *value = s_val;
     return s_ok != 0;
 }
 
@@ -72,19 +78,31 @@ __global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, 
     const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
     const u32 nthreads = gridDim.x * blockDim.x;
     const u32 warp = tid >> 5, nwarps = nthreads >> 5;
-    for (u64 v = tid; v < n; v += nthreads) dist[v] = kUnreached;
+    u64 maxdeg = 0;
+    for (u64 v = tid; v < n; v += nthreads) {
+        dist[v] = kUnreached;
+        const u64 d = off[v + 1] - off[v];
+        maxdeg = d > maxdeg ? d : maxdeg;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 y = __shfl_xor_sync(0xffffffffu, maxdeg, o);
+        maxdeg = y > maxdeg ? y : maxdeg;
+    }
+    if ((threadIdx.x & 31) == 0 && maxdeg) atomicMax(reinterpret_cast<unsigned long long*>(table + kTabMaxDeg), maxdeg);
     if (tid == 0)
         chunk_reset_all(table);
     if (!grid_barrier(ctl, table, gridDim.x)) return;
+    // without a vertex of degree >= kHeavyDeg no chunk is ever published
+    const bool chunks = ld_acq(table + kTabMaxDeg) >= kHeavyDeg;
     if (tid == 0) {
         dist[src] = 0;
         if (queue_enqueue<unsigned int, KIND>(qa, src, 0) == GQ_OK) st_rlx(ctl + kCtlFront0, 1);
     }
-    if (!grid_barrier(ctl, table, gridDim.x)) return;
+    u64 frontier = 0;
+    if (!grid_barrier(ctl, table, gridDim.x, ctl + kCtlFront0, &frontier)) return;
     u64 edges = 0, reached = 0;
     u32 level = 0;
     for (;; ++level) {
-        const u64 frontier = ld_acq(ctl + kCtlFront0 + level % 3);
         if (frontier == 0) break;
         reached += (tid == 0) ? frontier : 0;
         if (tid == 0) {
@@ -98,10 +116,10 @@ __global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, 
         const gq_dev& nxt = (level & 1) ? qa : qb;
         u32 cnt = 0;
         if (warp < dq) level_dequeue<KIND>(cur, nxt, c, &cnt, &edges);
-        if (!level_chunks<KIND>(nxt, c, &cnt, &edges) && (threadIdx.x & 31) == 0)
+        if (chunks && !level_chunks<KIND>(nxt, c, &cnt, &edges) && (threadIdx.x & 31) == 0)
             atomicCAS(reinterpret_cast<unsigned long long*>(ctl + kCtlErr), 0ull, 2ull);
         warp_add_full(reinterpret_cast<unsigned long long*>(ctl + kCtlFront0 + (level + 1) % 3), cnt);
-        if (!grid_barrier(ctl, table, gridDim.x)) return;
+        if (!grid_barrier(ctl, table, gridDim.x, ctl + kCtlFront0 + (level + 1) % 3, &frontier)) return;
     }
     if (stats) warp_add_full(stats + 2, edges);
     if (tid == 0 && stats) {
@@ -137,8 +155,11 @@ int launch_bfs(gq_handle ha, gq_handle hb, uint64_t n, const uint64_t* off, cons
         ha->aux_bytes = bytes;
     }
     u64* table = static_cast<u64*>(ha->aux);
-    // a search that ended on an expired barrier wait may have left the count behind
-    if (cudaMemsetAsync(table + kTabBarCount * kTabLine, 0, sizeof(u64), st) != cudaSuccess) return GQ_ERR_CUDA;
+    // a search that ended on an expired barrier wait may have left the count behind;
+    // the maximum degree is accumulated afresh by every search
+    if (cudaMemsetAsync(table + kTabBarCount * kTabLine, 0, sizeof(u64), st) != cudaSuccess ||
+        cudaMemsetAsync(table + kTabMaxDeg, 0, sizeof(u64), st) != cudaSuccess)
+        return GQ_ERR_CUDA;
     gq_dev qa = ha->dev, qb = hb->dev;
     const u64* o = reinterpret_cast<const u64*>(off);
     const u32* a = reinterpret_cast<const u32*>(adj);

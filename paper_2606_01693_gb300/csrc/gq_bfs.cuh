@@ -80,6 +80,8 @@ constexpr u64 kClusterChunkCap = 1u << 14;      // chunk-map positions of one cl
 constexpr u64 kTabLine = 512;                   // words per header line (4 KB)
 constexpr u64 kTabHeader = 6 * kTabLine;
 enum { kTabReserved = 0, kTabHanded = 1, kTabDone = 2, kTabTaken = 3, kTabBarCount = 4, kTabBarGen = 5 };
+// the graph's maximum degree (zero between searches), in the barrier-count line
+constexpr u64 kTabMaxDeg = kTabBarCount * kTabLine + 8;
 __host__ __device__ constexpr u64 chunk_map_bytes(u64 cap) { return (kTabHeader + cap) * sizeof(u64); }
 
 // Called by one thread before a search: clears the per-level counters.
@@ -317,7 +319,18 @@ __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* ta
                            const gq_bfs_instance& g, u32* dist, u32 ct, u32 nct, cg::cluster_group& cluster,
                            u64* edges, unsigned long long* err) {
     const u32 cw = ct >> 5, nwarps = nct >> 5;
-    for (u64 v = ct; v < g.n; v += nct) dist[v] = kUnreached;
+    const u64* off = reinterpret_cast<const u64*>(g.d_offsets);
+    u64 maxdeg = 0;
+    for (u64 v = ct; v < g.n; v += nct) {
+        dist[v] = kUnreached;
+        const u64 d = off[v + 1] - off[v];
+        maxdeg = d > maxdeg ? d : maxdeg;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 y = __shfl_xor_sync(kFull, maxdeg, o);
+        maxdeg = y > maxdeg ? y : maxdeg;
+    }
+    if ((threadIdx.x & 31) == 0 && maxdeg) atomicMax(reinterpret_cast<unsigned long long*>(table + kTabMaxDeg), maxdeg);
     if (ct == 0) {
         st_rlx(ctl + 0, 0);
         st_rlx(ctl + 1, 0);
@@ -330,6 +343,8 @@ __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* ta
         if (queue_enqueue<unsigned int, KIND>(qa, g.src, 0) == GQ_OK) st_rlx(ctl + 0, 1);
     }
     cluster.sync();
+    // without a vertex of degree >= kHeavyDeg no chunk is ever published
+    const bool chunks = ld_acq(table + kTabMaxDeg) >= kHeavyDeg;
     u32 level = 0;
     for (;; ++level) {
         const u64 frontier = ld_acq(ctl + level % 3);
@@ -346,7 +361,8 @@ __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* ta
         const gq_dev& nxt = (level & 1) ? qa : qb;
         u32 cnt = 0;
         if (cw < dq) level_dequeue<KIND>(cur, nxt, c, &cnt, edges);
-        if (!level_chunks<KIND>(nxt, c, &cnt, edges) && (threadIdx.x & 31) == 0 && err) atomicCAS(err, 0ull, 1ull);
+        if (chunks && !level_chunks<KIND>(nxt, c, &cnt, edges) && (threadIdx.x & 31) == 0 && err)
+            atomicCAS(err, 0ull, 1ull);
         warp_add_full(reinterpret_cast<unsigned long long*>(ctl + (level + 1) % 3), cnt);
         cluster.sync();
     }
@@ -355,6 +371,7 @@ __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* ta
         ymc_cluster_clear(qb, ct, nct, cluster);
     }
     cluster.sync();
+    if (ct == 0) st_rlx(table + kTabMaxDeg, 0);      // every thread read it before the last barrier
     return level;
 }
 
