@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, 
         const gq_dev& cur = (level & 1) ? qb : qa;
         const gq_dev& nxt = (level & 1) ? qa : qb;
         u32 cnt = 0;
-        if (warp < dq) level_dequeue<KIND>(cur, nxt, c, &cnt, &edges);
+        if (warp < dq) level_dequeue<KIND>(cur, nxt, c, warp, chunks, &cnt, &edges);
         if (chunks && !level_chunks<KIND>(nxt, c, &cnt, &edges) && (threadIdx.x & 31) == 0)
             atomicCAS(reinterpret_cast<unsigned long long*>(ctl + kCtlErr), 0ull, 2ull);
         warp_add_full(reinterpret_cast<unsigned long long*>(ctl + kCtlFront0 + (level + 1) % 3), cnt);

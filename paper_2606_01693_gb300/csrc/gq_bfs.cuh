@@ -72,9 +72,9 @@ constexpr u64 kClusterChunkCap = 1u << 14;      // chunk-map positions of one cl
 
 // Table memory: a header of six 4 KB lines, then the map itself (cap words, all
 // zero between levels: every written word is cleared by the warp that scans
-// it).  Header lines (three words each, rotating by level): reserved, handed,
-// done, taken; line 4 and 5 hold the whole-GPU search's barrier count and
-// generation.  Hot words on different 4 KB lines land in different L2 slices,
+// it).  Header lines 0-3 (three words each, rotating by level): reserved,
+// handed, done, taken; lines 4 and 5 hold the whole-GPU search's barrier count
+// and generation (and, in line 4, the graph's maximum degree).  Hot words on different 4 KB lines land in different L2 slices,
 // so the pollers of one word do not queue in front of the atomics on another.
 // A map word is (vertex << 32) | (chunk index + 1), or kSkipChunk.
 constexpr u64 kTabLine = 512;                   // words per header line (4 KB)
@@ -100,7 +100,7 @@ struct LevelCtx {
     u64* reserved;
     u64* handed;
     u64* done;
-    u64* taken;             // dequeues reserved this level
+    u64* taken;             // G-WFQ: dequeues reserved this level
     u64 frontier;           // items in the current frontier queue
     u64 dequeuers;          // warps that dequeue this level
 };
@@ -195,18 +195,27 @@ __device__ __forceinline__ bool chunk_publish(const LevelCtx& c, u32 v, u64 d) {
 }
 
 // Warp: phase 1 -- dequeue the frontier, gather light vertices, publish heavy
-// ones.  The level knows its frontier size F, so a lane first reserves one of
-// the F items (warp-aggregated fetch-add on `taken`) and only then dequeues:
-// every dequeue finds an item and none returns EMPTY.  (EMPTY dequeues would
-// cost a ticket each -- for G-WFQ-YMC a pool cell that the next level's
-// enqueuers would have to step over.)  A dequeue that fails anyway latches
-// GQ_ERR_INVALID in the queue.
+// ones.  The level knows its frontier size F, and its dequeuing warps are
+// warps 0 .. dequeuers-1: in round r, lane l of warp w does dequeue number
+// (r * dequeuers + w) * 32 + l if that is below F.  So exactly F dequeues run,
+// every one finds an item and none returns EMPTY (an EMPTY dequeue would cost a
+// ticket -- for G-WFQ-YMC a pool cell that the next level's enqueuers would
+// have to step over), with no counter to reserve them.  G-WFQ instead reserves
+// each dequeue with a warp-aggregated fetch-add on `taken` (also exactly F):
+// the fetch-add staggers the warps, and all of them arriving at once sent more
+// G-WFQ dequeues to the slow path (4096^2 grid 244 -> 354 ms).  A dequeue that
+// fails anyway latches GQ_ERR_INVALID in the queue.  With `chunked`, the warp
+// then counts itself in `done` for the chunk phase.
 template <int KIND>
-__device__ void level_dequeue(const gq_dev& cur, const gq_dev& nxt, const LevelCtx& c, u32* cnt, u64* edges) {
-    bool active = true;
-    for (u32 round = 0; round < kRetryLimit; ++round) {
+__device__ void level_dequeue(const gq_dev& cur, const gq_dev& nxt, const LevelCtx& c, u32 w, bool chunked,
+                              u32* cnt, u64* edges) {
+    const u32 lane = threadIdx.x & 31;
+    for (u64 round = 0;; ++round) {
+        bool active;
+        if constexpr (KIND == GQ_WFQ) active = warp_faa(c.taken, 1) < c.frontier;
+        else active = ((round * c.dequeuers + w) * 32 + lane) < c.frontier;
+        if (!__ballot_sync(kFull, active)) break;
         unsigned int v = 0;
-        if (active) active = warp_faa(c.taken, 1) < c.frontier;
         if (active) {
             const int s = queue_dequeue<unsigned int, KIND>(cur, &v, c.rec);
             if (s != GQ_OK) {
@@ -214,7 +223,6 @@ __device__ void level_dequeue(const gq_dev& cur, const gq_dev& nxt, const LevelC
                 active = false;
             }
         }
-        if (!__ballot_sync(kFull, active)) break;
         u64 b = 0, d = 0;
         if (active) {
             b = c.off[v];
@@ -223,8 +231,9 @@ __device__ void level_dequeue(const gq_dev& cur, const gq_dev& nxt, const LevelC
         }
         warp_gather<KIND>(nxt, c, b, d, cnt, edges);
     }
+    if (!chunked) return;
     __syncwarp();
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         __threadfence();                    // the chunk words are written before `done` counts this warp
         faa_rlx(c.done, 1);
     }
@@ -360,7 +369,7 @@ __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* ta
         const gq_dev& cur = (level & 1) ? qb : qa;
         const gq_dev& nxt = (level & 1) ? qa : qb;
         u32 cnt = 0;
-        if (cw < dq) level_dequeue<KIND>(cur, nxt, c, &cnt, edges);
+        if (cw < dq) level_dequeue<KIND>(cur, nxt, c, cw, chunks, &cnt, edges);
         if (chunks && !level_chunks<KIND>(nxt, c, &cnt, edges) && (threadIdx.x & 31) == 0 && err)
             atomicCAS(err, 0ull, 1ull);
         warp_add_full(reinterpret_cast<unsigned long long*>(ctl + (level + 1) % 3), cnt);
