@@ -45,7 +45,8 @@ typedef struct {
     uint32_t mode;                  /* GQ_SERVE_*                                              */
     uint32_t slots;                 /* persistent: clusters serving at once; 0 = all that fit  */
                                     /* on the GPU at once (fewer are used if fewer fit)       */
-    uint32_t cluster_blocks;        /* persistent: blocks of 256 threads per cluster: 1,2,4,8  */
+    uint32_t cluster_blocks;        /* persistent: blocks of 256 threads per cluster: 1, 2, 4,  */
+                                    /* 8 or 16 (16 is above the portable cluster size)         */
     uint64_t budget_bytes;          /* admission budget for per-request state                  */
     double wait_limit_s;            /* bound on any one wait of the device scheduler for its   */
                                     /* next request, and on the host's wait for progress;     */

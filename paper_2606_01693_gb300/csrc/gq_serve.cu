@@ -279,6 +279,9 @@ cudaError_t launch_serve(u32 slots, u32 cb, const gq_dev* views, const ServeK& a
 
 template <int KIND>
 cudaError_t max_clusters(u32 cb, int* out) {
+    // 16-block clusters exceed the portable cluster size and must be allowed
+    cudaError_t e = cudaFuncSetAttribute(k_serve<KIND>, cudaFuncAttributeNonPortableClusterSizeAllowed, cb > 8 ? 1 : 0);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cb);
     cfg.blockDim = dim3(256);
@@ -499,7 +502,7 @@ int validate(const gq_serve_config* c, const gq_serve_result* r) {
     if (c->kind != GQ_LFQ && c->kind != GQ_WFQ && c->kind != GQ_YMC) return GQ_ERR_INVALID;
     if (c->mode != GQ_SERVE_PERSISTENT && c->mode != GQ_SERVE_PER_REQUEST) return GQ_ERR_INVALID;
     if (c->mode == GQ_SERVE_PERSISTENT && c->cluster_blocks != 1 && c->cluster_blocks != 2 &&
-        c->cluster_blocks != 4 && c->cluster_blocks != 8)
+        c->cluster_blocks != 4 && c->cluster_blocks != 8 && c->cluster_blocks != 16)
         return GQ_ERR_INVALID;
     if (!c->ngraphs || !c->nrequests || !c->graphs || !c->req_graph || !c->req_src || !c->req_arrival_s)
         return GQ_ERR_INVALID;

@@ -59,6 +59,18 @@ def test_mix_matches_cpu_bfs(pool, kind, mode):
 
 
 @pytest.mark.parametrize("kind", KINDS)
+def test_sixteen_block_clusters(pool, kind):
+    """Clusters above the portable size (16 blocks of 256 threads) serve the same distances."""
+    host, dev = pool
+    gid, src, arr = synth.serving_requests([h[0] for h in host], 16, 5000.0, seed=44)
+    outs = _outs(host, gid)
+    r = gq.gq_serve(kind, dev, gid, src, arr, mode="persistent", slots=4, cluster_blocks=16, outs=outs)
+    assert r["slots_used"] >= 1 and (r["latency_s"] >= 0).all()
+    for o, w in zip(outs, _expected(host, gid, src)):
+        assert (o.cpu().numpy().view(np.uint32) == w).all()
+
+
+@pytest.mark.parametrize("kind", KINDS)
 def test_alone_equals_in_mix(pool, kind):
     """Each request served alone gives the bytes it gave in the mix (both modes)."""
     host, dev = pool
