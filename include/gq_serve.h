@@ -17,6 +17,12 @@
  *                         (the whole GPU, one request at a time), in arrival
  *                         order on one stream; completion is an event the host
  *                         polls.
+ *   GQ_SERVE_ADAPTIVE     per-request launches while few requests wait; when
+ *                         switch_backlog launched requests are still pending,
+ *                         the persistent scheduler is started (after them, on
+ *                         the same stream) and takes the following requests;
+ *                         after 0.5 ms with nothing to do it is stopped and
+ *                         per-request launches resume.
  * Admission (both modes, first come first served): a request is published or
  * launched only when its device state fits in the budget; it waits on the host
  * otherwise.  A request's state is counted as its graph's CSR (8 (n + 1) +
@@ -38,14 +44,14 @@
 extern "C" {
 #endif
 
-enum { GQ_SERVE_PERSISTENT = 0, GQ_SERVE_PER_REQUEST = 1 };
+enum { GQ_SERVE_PERSISTENT = 0, GQ_SERVE_PER_REQUEST = 1, GQ_SERVE_ADAPTIVE = 2 };
 
 typedef struct {
     int32_t kind;                   /* frontier queue kind (gq_kind)                           */
     uint32_t mode;                  /* GQ_SERVE_*                                              */
-    uint32_t slots;                 /* persistent: clusters serving at once; 0 = all that fit  */
-                                    /* on the GPU at once (fewer are used if fewer fit)       */
-    uint32_t cluster_blocks;        /* persistent: blocks of 256 threads per cluster: 1, 2, 4,  */
+    uint32_t slots;                 /* persistent / adaptive: clusters serving at once; 0 = all */
+                                    /* that fit on the GPU at once (fewer if fewer fit)       */
+    uint32_t cluster_blocks;        /* persistent / adaptive: blocks of 256 threads per cluster: 1, 2, 4, */
                                     /* 8 or 16 (16 is above the portable cluster size)         */
     uint64_t budget_bytes;          /* admission budget for per-request state                  */
     double wait_limit_s;            /* bound on any one wait of the device scheduler for its   */
@@ -62,6 +68,9 @@ typedef struct {
                                     /* uint32, GQ_BFS_UNREACHED where unreached); null entries */
                                     /* (or a null array) use scratch from a device arena of at */
                                     /* most budget_bytes                                      */
+    uint32_t switch_backlog;        /* adaptive: pending launches that start the scheduler;   */
+                                    /* 0 = 8                                                   */
+    uint32_t reserved;
 } gq_serve_config;
 
 typedef struct {
@@ -69,8 +78,9 @@ typedef struct {
     double wall_s;                  /* first arrival to last completion                        */
     uint64_t peak_state_bytes;      /* largest admitted state counted at one time              */
     uint64_t admission_waits;       /* requests that had arrived but waited for budget         */
-    uint64_t edges_scanned;         /* persistent mode: edges scanned over all requests        */
-    uint32_t slots_used;            /* persistent mode: clusters launched                      */
+    uint64_t edges_scanned;         /* by the persistent scheduler, over all its requests      */
+    uint64_t persistent_requests;   /* requests the persistent scheduler served                */
+    uint32_t slots_used;            /* clusters of the persistent scheduler (0: not used)      */
     int32_t status;                 /* GQ_OK or the first error                                */
 } gq_serve_result;
 

@@ -104,7 +104,8 @@ def run_serve(args) -> None:
                               "p50_ms": round(float(np.percentile(lat, 50)), 3),
                               "p99_ms": round(float(np.percentile(lat, 99)), 3),
                               "throughput_rps": round(args.requests / r["wall_s"], 1),
-                              "admission_waits": int(r["admission_waits"]), "slots": int(r["slots_used"])}),
+                              "admission_waits": int(r["admission_waits"]), "slots": int(r["slots_used"]),
+                              "persistent_requests": int(r["persistent_requests"])}),
                   flush=True)
 
 
@@ -127,7 +128,7 @@ def main(argv=None) -> None:
     s.add_argument("--max-scale", type=int, default=20)
     s.add_argument("--rate", type=float, default=1000.0)
     s.add_argument("--requests", type=int, default=1000)
-    s.add_argument("--modes", default="persistent,per_request")
+    s.add_argument("--modes", default="persistent,per_request,adaptive")
     s.add_argument("--cluster-blocks", type=int, default=8)
     s.add_argument("--budget-gib", type=float, default=32.0)
     for q in (b, r, s):

@@ -26,6 +26,8 @@
 
 #include <chrono>
 #include <cstring>
+#include <deque>
+#include <algorithm>
 #include <iterator>
 #include <map>
 #include <vector>
@@ -295,174 +297,289 @@ cudaError_t max_clusters(u32 cb, int* out) {
     return cudaOccupancyMaxActiveClusters(out, k_serve<KIND>, &cfg);
 }
 
-// RAII for the device and mapped allocations of one gq_serve call.
+// The stream and the distance arena of one gq_serve call.
 struct Buffers {
-    void* dev = nullptr;      // claim, per-slot control words, stats, views, graphs
-    void* mapped = nullptr;   // ring + shared words
     char* arena = nullptr;
     cudaStream_t st = nullptr;
-    std::vector<cudaEvent_t> ev;
     ~Buffers() {
         if (st) cudaStreamSynchronize(st);
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        if (dev) cudaFree(dev);
         if (arena) cudaFree(arena);
-        if (mapped) cudaFreeHost(mapped);
         if (st) cudaStreamDestroy(st);
     }
 };
 
-int serve_persistent(Runtime& rt, Buffers& b, u64 nmax) {
-    const gq_serve_config& c = rt.c;
-    const u32 cb = c.cluster_blocks;
-    int fit = 0;
-    cudaError_t e = c.kind == GQ_LFQ ? max_clusters<GQ_LFQ>(cb, &fit)
-                    : c.kind == GQ_WFQ ? max_clusters<GQ_WFQ>(cb, &fit)
-                                       : max_clusters<GQ_YMC>(cb, &fit);
-    if (e != cudaSuccess || fit < 1) return GQ_ERR_CUDA;
-    u32 slots = c.slots ? c.slots : (u32)fit;
-    if (slots > (u32)fit) slots = (u32)fit;
-    if ((u64)slots > c.nrequests) slots = c.nrequests;
-    rt.r.slots_used = slots;
-
+// One persistent scheduler launch and everything it uses: 2 * slots frontier
+// queues, the mapped request ring and shared words, and a device block (ticket
+// counter | 64 B control per slot | stats | chunk maps | queue views | graph
+// table).  A run of the scheduler is an "episode": tickets restart at 0, the
+// host publishes requests in ticket order, and the clusters leave when their
+// ticket reaches the episode's limit or the host raises the stop word.
+struct Persistent {
+    const gq_serve_config& c;
+    u32 slots = 0;
     Queues fr;
-    int s = fr.create(2ull * slots, c.kind, queue_capacity(c.kind, nmax), cb * 256, b.st);
-    if (s != GQ_OK) return s;
-
-    u64 ring_n = 1;
-    while (ring_n < c.nrequests && ring_n < 4096) ring_n <<= 1;
-    const u64 ring_bytes = ring_n * sizeof(ServeEntry);
-    if (cudaHostAlloc(&b.mapped, ring_bytes + sizeof(ServeShared), cudaHostAllocMapped) != cudaSuccess)
-        return GQ_ERR_NOMEM;
-    std::memset(b.mapped, 0, ring_bytes + sizeof(ServeShared));
-    ServeEntry* ring = static_cast<ServeEntry*>(b.mapped);
-    ServeShared* sh = reinterpret_cast<ServeShared*>(static_cast<char*>(b.mapped) + ring_bytes);
-    void* d_mapped = nullptr;
-    if (cudaHostGetDevicePointer(&d_mapped, b.mapped, 0) != cudaSuccess) return GQ_ERR_CUDA;
-
-    // device block: claim (256 B) | ctl 64 B per slot | stats | chunk maps | views | graphs
-    const u64 o_ctl = 256, o_stats = round256(o_ctl + 64ull * slots), o_tables = o_stats + 256,
-              o_views = round256(o_tables + slots * chunk_map_bytes(kClusterChunkCap)),
-              o_graphs = round256(o_views + 2ull * slots * sizeof(gq_dev)),
-              total = round256(o_graphs + (u64)c.ngraphs * sizeof(gq_bfs_instance));
-    if (cudaMalloc(&b.dev, total) != cudaSuccess) return GQ_ERR_NOMEM;
-    char* d = static_cast<char*>(b.dev);
-    std::vector<gq_dev> views(2ull * slots);
-    for (u64 i = 0; i < views.size(); ++i) views[i] = fr.h[i]->dev;
-    if (cudaMemsetAsync(d, 0, o_views, b.st) != cudaSuccess ||
-        cudaMemcpyAsync(d + o_views, views.data(), views.size() * sizeof(gq_dev), cudaMemcpyHostToDevice, b.st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(d + o_graphs, c.graphs, (u64)c.ngraphs * sizeof(gq_bfs_instance), cudaMemcpyHostToDevice,
-                        b.st) != cudaSuccess ||
-        cudaStreamSynchronize(b.st) != cudaSuccess)
-        return GQ_ERR_CUDA;
-
+    void* dev = nullptr;
+    void* mapped = nullptr;
+    ServeEntry* ring = nullptr;
+    ServeShared* sh = nullptr;
+    u64 ring_n = 0;
+    char* d = nullptr;
+    u64 o_stats = 0;
     ServeK a;
-    a.ring = static_cast<ServeEntry*>(d_mapped);
-    a.sh = reinterpret_cast<ServeShared*>(static_cast<char*>(d_mapped) + ring_bytes);
-    a.graphs = reinterpret_cast<const gq_bfs_instance*>(d + o_graphs);
-    a.ngraphs = c.ngraphs;
-    a.ring_mask = (u32)(ring_n - 1);
-    a.nreq = c.nrequests;
-    a.claim = reinterpret_cast<u64*>(d);
-    a.ctl = reinterpret_cast<u64*>(d + o_ctl);
-    a.stats = reinterpret_cast<unsigned long long*>(d + o_stats);
-    a.tables = reinterpret_cast<u64*>(d + o_tables);
-    const double limit = c.wait_limit_s > 0 ? c.wait_limit_s : 30.0;
-    a.wait_ns = (u64)(limit * 1e9);
-    const gq_dev* dv = reinterpret_cast<const gq_dev*>(d + o_views);
-    e = c.kind == GQ_LFQ ? launch_serve<GQ_LFQ>(slots, cb, dv, a, b.st)
-        : c.kind == GQ_WFQ ? launch_serve<GQ_WFQ>(slots, cb, dv, a, b.st)
-                           : launch_serve<GQ_YMC>(slots, cb, dv, a, b.st);
-    if (e != cudaSuccess) return GQ_ERR_CUDA;
+    const gq_dev* dv = nullptr;
+    cudaEvent_t ended = nullptr;
+    bool running = false, stopping = false;
+    u64 next_ticket = 0;
+    std::vector<u64> entry_req;     // ring entry -> request whose ticket it holds
+    std::vector<char> entry_busy;   // ring entry holds a ticket not yet seen done
+    std::vector<u64> inflight;      // published tickets not yet seen done
 
-    rt.t0 = Clock::now();
-    const u64 n = c.nrequests;
-    u64 next = 0, done = 0;
-    std::vector<u64> inflight;
-    double last_progress = 0;
-    int err = GQ_OK;
-    for (u64 iter = 0; done < n; ++iter) {
-        double t = rt.now();
-        while (next < n && c.req_arrival_s[next] <= t) {
-            if (next >= ring_n && !rt.finished[next - ring_n]) break;   // ring entry still in use
-            u32* dist = nullptr;
-            if (!rt.admit(next, &dist)) {
-                if (!rt.waited[next]) {
-                    rt.waited[next] = 1;
-                    ++rt.r.admission_waits;
-                }
-                break;
-            }
-            ServeEntry* en = ring + (next & (ring_n - 1));
-            en->req = (u64)c.req_graph[next] | ((u64)c.req_src[next] << 32);
-            en->dist = reinterpret_cast<u64>(dist);
-            en->levels = 0;
-            __atomic_store_n(&en->seq, next + 1, __ATOMIC_RELEASE);
-            inflight.push_back(next);
-            ++next;
+    explicit Persistent(const gq_serve_config& cfg) : c(cfg) {}
+    ~Persistent() {
+        if (ended) cudaEventDestroy(ended);
+        if (dev) cudaFree(dev);
+        if (mapped) cudaFreeHost(mapped);
+    }
+
+    int init(u64 nmax, cudaStream_t st) {
+        const u32 cb = c.cluster_blocks;
+        int fit = 0;
+        cudaError_t e = c.kind == GQ_LFQ ? max_clusters<GQ_LFQ>(cb, &fit)
+                        : c.kind == GQ_WFQ ? max_clusters<GQ_WFQ>(cb, &fit)
+                                           : max_clusters<GQ_YMC>(cb, &fit);
+        if (e != cudaSuccess || fit < 1) return GQ_ERR_CUDA;
+        slots = c.slots ? c.slots : (u32)fit;
+        if (slots > (u32)fit) slots = (u32)fit;
+        if ((u64)slots > c.nrequests) slots = c.nrequests;
+        int s = fr.create(2ull * slots, c.kind, queue_capacity(c.kind, nmax), cb * 256, st);
+        if (s != GQ_OK) return s;
+
+        ring_n = 1;
+        while (ring_n < c.nrequests && ring_n < 4096) ring_n <<= 1;
+        const u64 ring_bytes = ring_n * sizeof(ServeEntry);
+        if (cudaHostAlloc(&mapped, ring_bytes + sizeof(ServeShared), cudaHostAllocMapped) != cudaSuccess) {
+            mapped = nullptr;
+            return GQ_ERR_NOMEM;
         }
-        t = rt.now();
+        std::memset(mapped, 0, ring_bytes + sizeof(ServeShared));
+        ring = static_cast<ServeEntry*>(mapped);
+        sh = reinterpret_cast<ServeShared*>(static_cast<char*>(mapped) + ring_bytes);
+        void* d_mapped = nullptr;
+        if (cudaHostGetDevicePointer(&d_mapped, mapped, 0) != cudaSuccess) return GQ_ERR_CUDA;
+        entry_req.assign(ring_n, 0);
+        entry_busy.assign(ring_n, 0);
+
+        const u64 o_ctl = 256;
+        o_stats = round256(o_ctl + 64ull * slots);
+        const u64 o_tables = o_stats + 256,
+                  o_views = round256(o_tables + slots * chunk_map_bytes(kClusterChunkCap)),
+                  o_graphs = round256(o_views + 2ull * slots * sizeof(gq_dev)),
+                  total = round256(o_graphs + (u64)c.ngraphs * sizeof(gq_bfs_instance));
+        if (cudaMalloc(&dev, total) != cudaSuccess) {
+            dev = nullptr;
+            return GQ_ERR_NOMEM;
+        }
+        d = static_cast<char*>(dev);
+        std::vector<gq_dev> views(2ull * slots);
+        for (u64 i = 0; i < views.size(); ++i) views[i] = fr.h[i]->dev;
+        if (cudaMemsetAsync(d, 0, o_views, st) != cudaSuccess ||
+            cudaMemcpyAsync(d + o_views, views.data(), views.size() * sizeof(gq_dev), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(d + o_graphs, c.graphs, (u64)c.ngraphs * sizeof(gq_bfs_instance),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return GQ_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&ended, cudaEventDisableTiming) != cudaSuccess) return GQ_ERR_CUDA;
+        a.ring = static_cast<ServeEntry*>(d_mapped);
+        a.sh = reinterpret_cast<ServeShared*>(static_cast<char*>(d_mapped) + ring_bytes);
+        a.graphs = reinterpret_cast<const gq_bfs_instance*>(d + o_graphs);
+        a.ngraphs = c.ngraphs;
+        a.ring_mask = (u32)(ring_n - 1);
+        a.nreq = 0;
+        a.claim = reinterpret_cast<u64*>(d);
+        a.ctl = reinterpret_cast<u64*>(d + o_ctl);
+        a.stats = reinterpret_cast<unsigned long long*>(d + o_stats);
+        a.tables = reinterpret_cast<u64*>(d + o_tables);
+        a.wait_ns = (u64)((c.wait_limit_s > 0 ? c.wait_limit_s : 30.0) * 1e9);
+        dv = reinterpret_cast<const gq_dev*>(d + o_views);
+        return GQ_OK;
+    }
+
+    // Launches an episode whose clusters leave once `limit` tickets are claimed.
+    int start(u64 limit, cudaStream_t st) {
+        for (u64 e = 0; e < ring_n; ++e) {
+            ring[e].seq = 0;
+            ring[e].done = 0;
+        }
+        __atomic_store_n(&sh->stop, 0ull, __ATOMIC_RELEASE);
+        if (cudaMemsetAsync(a.claim, 0, sizeof(u64), st) != cudaSuccess) return GQ_ERR_CUDA;
+        a.nreq = limit;
+        const cudaError_t e = c.kind == GQ_LFQ ? launch_serve<GQ_LFQ>(slots, c.cluster_blocks, dv, a, st)
+                              : c.kind == GQ_WFQ ? launch_serve<GQ_WFQ>(slots, c.cluster_blocks, dv, a, st)
+                                                 : launch_serve<GQ_YMC>(slots, c.cluster_blocks, dv, a, st);
+        if (e != cudaSuccess || cudaEventRecord(ended, st) != cudaSuccess) return GQ_ERR_CUDA;
+        running = true;
+        stopping = false;
+        next_ticket = 0;
+        std::fill(entry_busy.begin(), entry_busy.end(), 0);
+        return GQ_OK;
+    }
+
+    bool can_publish() const { return running && !stopping && !entry_busy[next_ticket & (ring_n - 1)]; }
+
+    // Publishes request i (distances to dist) as the next ticket.
+    void publish(u64 i, u32* dist) {
+        const u64 t = next_ticket++;
+        const u64 e = t & (ring_n - 1);
+        ServeEntry* en = ring + e;
+        en->req = (u64)c.req_graph[i] | ((u64)c.req_src[i] << 32);
+        en->dist = reinterpret_cast<u64>(dist);
+        en->levels = 0;
+        entry_req[e] = i;
+        entry_busy[e] = 1;
+        __atomic_store_n(&en->seq, t + 1, __ATOMIC_RELEASE);
+        inflight.push_back(t);
+    }
+
+    // Reports every published ticket now done (done(request, bad) for each).
+    template <class F>
+    void poll(F done) {
         for (u64 k = 0; k < inflight.size();) {
-            const u64 i = inflight[k];
-            ServeEntry* en = ring + (i & (ring_n - 1));
-            if (__atomic_load_n(&en->done, __ATOMIC_ACQUIRE) == i + 1) {
-                rt.complete(i, t);
-                ++done;
-                last_progress = t;
-                if (en->levels == ~0ull && err == GQ_OK) err = GQ_ERR_INVALID;
+            const u64 t = inflight[k];
+            ServeEntry* en = ring + (t & (ring_n - 1));
+            if (__atomic_load_n(&en->done, __ATOMIC_ACQUIRE) == t + 1) {
+                entry_busy[t & (ring_n - 1)] = 0;
+                done(entry_req[t & (ring_n - 1)], en->levels == ~0ull);
                 inflight[k] = inflight.back();
                 inflight.pop_back();
             } else {
                 ++k;
             }
         }
-        if (done == n) break;
-        if ((iter & 1023) == 1023) {
-            const cudaError_t q = cudaStreamQuery(b.st);
-            if (q != cudaErrorNotReady) {   // the scheduler ended with requests outstanding
-                err = q != cudaSuccess ? GQ_ERR_CUDA : GQ_ERR_TIMEOUT;
-                break;
-            }
-            const double waiting_since = next < n && c.req_arrival_s[next] > last_progress ? c.req_arrival_s[next]
-                                                                                              : last_progress;
-            if (inflight.size() && t - waiting_since > limit + 5.0) {
-                err = GQ_ERR_TIMEOUT;
-                break;
-            }
-        }
     }
-    __atomic_store_n(&sh->stop, 1ull, __ATOMIC_RELEASE);
-    if (cudaStreamSynchronize(b.st) != cudaSuccess) return GQ_ERR_CUDA;
-    unsigned long long st2[3] = {0, 0, 0};
-    if (cudaMemcpy(st2, d + o_stats, sizeof(st2), cudaMemcpyDeviceToHost) != cudaSuccess) return GQ_ERR_CUDA;
-    if (st2[2]) return st2[2] == 2 ? GQ_ERR_INVALID : GQ_ERR_TIMEOUT;
-    if (err != GQ_OK) return err;
-    rt.r.edges_scanned = st2[0];
-    if (st2[1] != n) return GQ_ERR_TIMEOUT;
-    return fr.status(b.st);
-}
 
-int serve_per_request(Runtime& rt, Buffers& b, u64 nmax) {
-    const gq_serve_config& c = rt.c;
+    // Asks the clusters to leave at their next wait (only with nothing in flight,
+    // so that no published ticket is left unclaimed).
+    void stop() {
+        __atomic_store_n(&sh->stop, 1ull, __ATOMIC_RELEASE);
+        stopping = true;
+    }
+
+    // 1 if the episode's kernel has ended, 0 if it runs, < 0 on a CUDA error.
+    int ended_yet() {
+        const cudaError_t q = cudaEventQuery(ended);
+        if (q == cudaErrorNotReady) return 0;
+        if (q != cudaSuccess) return GQ_ERR_CUDA;
+        running = stopping = false;
+        return 1;
+    }
+
+    // Device error word and edge count (after the last episode ended).
+    int finish(gq_serve_result& r, cudaStream_t st) {
+        unsigned long long st3[3] = {0, 0, 0};
+        if (cudaStreamSynchronize(st) != cudaSuccess ||
+            cudaMemcpy(st3, d + o_stats, sizeof(st3), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return GQ_ERR_CUDA;
+        r.edges_scanned = st3[0];
+        r.persistent_requests = st3[1];
+        if (st3[2]) return st3[2] == 2 ? GQ_ERR_INVALID : GQ_ERR_TIMEOUT;
+        return fr.status(st);
+    }
+};
+
+// One gq_bfs launch per request (the whole GPU), in order on one stream.
+struct PerRequest {
+    const gq_serve_config& c;
     Queues fr;
-    // gq_bfs runs one thread per resident slot of the GPU (at most max_threads)
-    int s = fr.create(2, c.kind, queue_capacity(c.kind, nmax), 1u << 19, b.st);
-    if (s != GQ_OK) return s;
-    if (cudaStreamSynchronize(b.st) != cudaSuccess) return GQ_ERR_CUDA;
+    std::vector<cudaEvent_t> ev;
+    std::deque<u64> pending;        // launched requests, in launch (= completion) order
+    u64 launched = 0;
+
+    explicit PerRequest(const gq_serve_config& cfg) : c(cfg) {}
+    ~PerRequest() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    int init(u64 nmax, cudaStream_t st) {
+        // gq_bfs runs one thread per resident slot of the GPU (at most max_threads)
+        int s = fr.create(2, c.kind, queue_capacity(c.kind, nmax), 1u << 19, st);
+        if (s != GQ_OK) return s;
+        const u64 nev = c.nrequests < 1024 ? c.nrequests : 1024;
+        ev.assign(nev, nullptr);
+        for (u64 i = 0; i < nev; ++i)
+            if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) return GQ_ERR_CUDA;
+        return cudaStreamSynchronize(st) == cudaSuccess ? GQ_OK : GQ_ERR_CUDA;
+    }
+    bool can_launch() const { return pending.size() < ev.size(); }
+    int launch(u64 i, u32* dist, cudaStream_t st) {
+        const gq_bfs_instance& g = c.graphs[c.req_graph[i]];
+        if (c.kind == GQ_YMC && (gq_reset(fr.h[0], st) != GQ_OK || gq_reset(fr.h[1], st) != GQ_OK))
+            return GQ_ERR_CUDA;
+        const int s = gq_bfs(fr.h[0], fr.h[1], g.n, g.d_offsets, g.d_adj, c.req_src[i], dist, nullptr, st);
+        if (s != GQ_OK) return s;
+        if (cudaEventRecord(ev[launched % ev.size()], st) != cudaSuccess) return GQ_ERR_CUDA;
+        ++launched;
+        pending.push_back(i);
+        return GQ_OK;
+    }
+    // Reports requests now done, in order; < 0 on a CUDA error.
+    template <class F>
+    int poll(F done) {
+        while (!pending.empty()) {
+            const cudaError_t q = cudaEventQuery(ev[(launched - pending.size()) % ev.size()]);
+            if (q == cudaErrorNotReady) break;
+            if (q != cudaSuccess) return GQ_ERR_CUDA;
+            const u64 i = pending.front();
+            pending.pop_front();
+            done(i);
+        }
+        return GQ_OK;
+    }
+};
+
+// The host loop shared by the three modes.  Requests are started in arrival
+// order (first come, first served) once admitted; `route` says where the next
+// one goes.
+int serve_loop(Runtime& rt, cudaStream_t st, u64 nmax) {
+    const gq_serve_config& c = rt.c;
     const u64 n = c.nrequests;
-    const u64 nev = n < 1024 ? n : 1024;
-    b.ev.assign(nev, nullptr);
-    for (u64 i = 0; i < nev; ++i)
-        if (cudaEventCreateWithFlags(&b.ev[i], cudaEventDisableTiming) != cudaSuccess) return GQ_ERR_CUDA;
+    const double limit = c.wait_limit_s > 0 ? c.wait_limit_s : 30.0;
+    const bool use_p = c.mode != GQ_SERVE_PER_REQUEST, use_r = c.mode != GQ_SERVE_PERSISTENT;
+    Persistent P(c);
+    PerRequest R(c);
+    int s = GQ_OK;
+    if (use_p && (s = P.init(nmax, st)) != GQ_OK) return s;
+    if (use_r && (s = R.init(nmax, st)) != GQ_OK) return s;
+    rt.r.slots_used = use_p ? P.slots : 0;
+    // adaptive: the persistent scheduler takes over when this many launched
+    // requests are still waiting on the stream, and hands back after idling
+    const u64 switch_backlog = c.switch_backlog ? c.switch_backlog : 8;
+    const double idle_s = 0.5e-3;
 
     rt.t0 = Clock::now();
-    const double limit = c.wait_limit_s > 0 ? c.wait_limit_s : 30.0;
+    if (c.mode == GQ_SERVE_PERSISTENT && (s = P.start(n, st)) != GQ_OK) return s;
     u64 next = 0, done = 0;
-    double last_progress = 0;
-    while (done < n) {
-        double t = rt.now();
-        while (next < n && c.req_arrival_s[next] <= t && next - done < nev) {
+    double last_progress = 0, idle_since = 0;
+    int err = GQ_OK;
+    auto finished = [&](u64 i) {
+        rt.complete(i, rt.now());
+        ++done;
+        last_progress = rt.now();
+    };
+    for (u64 iter = 0; done < n && err == GQ_OK; ++iter) {
+        const double t = rt.now();
+        // start arrived requests in order
+        while (next < n && c.req_arrival_s[next] <= t) {
+            bool to_p = c.mode == GQ_SERVE_PERSISTENT;
+            if (c.mode == GQ_SERVE_ADAPTIVE) {
+                if (P.running && !P.stopping) to_p = true;
+                else if (!P.running && R.pending.size() >= switch_backlog) {
+                    if ((err = P.start(~0ull, st)) != GQ_OK) break;
+                    to_p = true;
+                } else if (P.running) {
+                    break;                                 // stopping: wait for the scheduler to leave
+                }
+            }
+            if (to_p ? !P.can_publish() : !R.can_launch()) break;
             u32* dist = nullptr;
             if (!rt.admit(next, &dist)) {
                 if (!rt.waited[next]) {
@@ -471,37 +588,70 @@ int serve_per_request(Runtime& rt, Buffers& b, u64 nmax) {
                 }
                 break;
             }
-            const gq_bfs_instance& g = c.graphs[c.req_graph[next]];
-            if (c.kind == GQ_YMC && (gq_reset(fr.h[0], b.st) != GQ_OK || gq_reset(fr.h[1], b.st) != GQ_OK))
-                return GQ_ERR_CUDA;
-            s = gq_bfs(fr.h[0], fr.h[1], g.n, g.d_offsets, g.d_adj, c.req_src[next], dist, nullptr, b.st);
-            if (s != GQ_OK) return s;
-            if (cudaEventRecord(b.ev[next % nev], b.st) != cudaSuccess) return GQ_ERR_CUDA;
+            if (to_p) {
+                P.publish(next, dist);
+            } else if ((err = R.launch(next, dist, st)) != GQ_OK) {
+                break;
+            }
             ++next;
         }
-        // one stream: requests complete in submission order
-        while (done < next) {
-            const cudaError_t q = cudaEventQuery(b.ev[done % nev]);
-            if (q == cudaErrorNotReady) break;
-            if (q != cudaSuccess) return GQ_ERR_CUDA;
-            t = rt.now();
-            rt.complete(done, t);
-            ++done;
-            last_progress = t;
+        if (err != GQ_OK) break;
+        // completions
+        if (use_p)
+            P.poll([&](u64 i, bool bad) {
+                if (bad && err == GQ_OK) err = GQ_ERR_INVALID;
+                finished(i);
+            });
+        if (use_r && (s = R.poll(finished)) != GQ_OK) {
+            err = s;
+            break;
         }
-        if (done < next && rt.now() - last_progress > limit + 5.0 &&
-            rt.now() - c.req_arrival_s[done] > limit + 5.0)
-            return GQ_ERR_TIMEOUT;
+        // adaptive: an idle scheduler hands back to per-request launches
+        if (c.mode == GQ_SERVE_ADAPTIVE && P.running) {
+            if (!P.stopping) {
+                const bool idle = P.inflight.empty() && (next == n || c.req_arrival_s[next] > rt.now());
+                if (!idle) {
+                    idle_since = rt.now();
+                } else if (rt.now() - idle_since > idle_s) {
+                    P.stop();
+                }
+            }
+            if (P.stopping && (s = P.ended_yet()) < 0) err = s;
+        }
+        if ((iter & 1023) == 1023 && c.mode == GQ_SERVE_PERSISTENT && P.running) {
+            const int e = P.ended_yet();
+            if (e < 0) {
+                err = e;
+            } else if (e == 1) {             // ended: every request it served is done now
+                P.poll([&](u64 i, bool bad) {
+                    if (bad && err == GQ_OK) err = GQ_ERR_INVALID;
+                    finished(i);
+                });
+                if (done < n && err == GQ_OK) err = GQ_ERR_TIMEOUT;
+            }
+        }
+        if ((iter & 1023) == 1023 && done < next) {
+            const double now = rt.now();
+            if (now - last_progress > limit + 5.0 && now - c.req_arrival_s[done < n ? done : n - 1] > limit + 5.0)
+                err = GQ_ERR_TIMEOUT;
+        }
     }
-    if (cudaStreamSynchronize(b.st) != cudaSuccess) return GQ_ERR_CUDA;
-    return fr.status(b.st);
+    if (use_p) {
+        if (P.running) P.stop();
+        const int f = P.finish(rt.r, st);
+        if (err == GQ_OK && f != GQ_OK) err = f;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess && err == GQ_OK) err = GQ_ERR_CUDA;
+    if (use_r && err == GQ_OK) err = R.fr.status(st);
+    return err;
 }
 
 int validate(const gq_serve_config* c, const gq_serve_result* r) {
     if (!c || !r || !r->latency_s) return GQ_ERR_INVALID;
     if (c->kind != GQ_LFQ && c->kind != GQ_WFQ && c->kind != GQ_YMC) return GQ_ERR_INVALID;
-    if (c->mode != GQ_SERVE_PERSISTENT && c->mode != GQ_SERVE_PER_REQUEST) return GQ_ERR_INVALID;
-    if (c->mode == GQ_SERVE_PERSISTENT && c->cluster_blocks != 1 && c->cluster_blocks != 2 &&
+    if (c->mode != GQ_SERVE_PERSISTENT && c->mode != GQ_SERVE_PER_REQUEST && c->mode != GQ_SERVE_ADAPTIVE)
+        return GQ_ERR_INVALID;
+    if (c->mode != GQ_SERVE_PER_REQUEST && c->cluster_blocks != 1 && c->cluster_blocks != 2 &&
         c->cluster_blocks != 4 && c->cluster_blocks != 8 && c->cluster_blocks != 16)
         return GQ_ERR_INVALID;
     if (!c->ngraphs || !c->nrequests || !c->graphs || !c->req_graph || !c->req_src || !c->req_arrival_s)
@@ -526,7 +676,7 @@ extern "C" int gq_serve(const gq_serve_config* cfg, gq_serve_result* res) {
     if (s != GQ_OK) return s;
     const gq_serve_config& c = *cfg;
     res->wall_s = 0;
-    res->peak_state_bytes = res->admission_waits = res->edges_scanned = 0;
+    res->peak_state_bytes = res->admission_waits = res->edges_scanned = res->persistent_requests = 0;
     res->slots_used = 0;
     res->status = GQ_OK;
     for (u32 i = 0; i < c.nrequests; ++i) res->latency_s[i] = -1.0;
@@ -534,6 +684,7 @@ extern "C" int gq_serve(const gq_serve_config* cfg, gq_serve_result* res) {
     // per-graph state: CSR bytes need m = offsets[n], read once from the device
     std::vector<u64> graph_charge(c.ngraphs), graph_dist(c.ngraphs);
     u64 nmax = 1;
+    // queue records counted as the per-request form needs them (the larger), except in pure persistent mode
     const u32 mt = c.mode == GQ_SERVE_PERSISTENT ? c.cluster_blocks * 256 : (1u << 19);
     for (u32 g = 0; g < c.ngraphs; ++g) {
         const gq_bfs_instance& x = c.graphs[g];
@@ -567,9 +718,12 @@ extern "C" int gq_serve(const gq_serve_config* cfg, gq_serve_result* res) {
 
     Buffers b;
     if (cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking) != cudaSuccess) return res->status = GQ_ERR_CUDA;
-    if (arena_size && cudaMalloc(&b.arena, arena_size) != cudaSuccess) return res->status = GQ_ERR_NOMEM;
+    if (arena_size && cudaMalloc(&b.arena, arena_size) != cudaSuccess) {
+        b.arena = nullptr;
+        return res->status = GQ_ERR_NOMEM;
+    }
     rt.d_arena = b.arena;
-    s = c.mode == GQ_SERVE_PERSISTENT ? serve_persistent(rt, b, nmax) : serve_per_request(rt, b, nmax);
+    s = serve_loop(rt, b.st, nmax);
     double last = 0;
     for (u32 i = 0; i < c.nrequests; ++i)
         if (rt.finished[i] && c.req_arrival_s[i] + res->latency_s[i] > last)

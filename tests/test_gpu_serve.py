@@ -12,7 +12,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 KINDS = list(gq.READY_KINDS)
-MODES = ["persistent", "per_request"]
+MODES = ["persistent", "per_request", "adaptive"]
 
 
 @pytest.fixture(scope="module")
@@ -107,6 +107,24 @@ def test_admission_waits_under_small_budget(pool, mode):
     outs = _outs(host, gid)
     r = gq.gq_serve("lfq", dev, gid, src, arr, mode=mode, slots=8, cluster_blocks=2, budget_bytes=budget,
                     outs=outs)
+    for o, w in zip(outs, _expected(host, gid, src)):
+        assert (o.cpu().numpy().view(np.uint32) == w).all()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_adaptive_switches_both_ways(pool, kind):
+    """A burst hands the requests to the persistent scheduler; after a quiet gap
+    per-request launches serve the rest; every result equals the oracle's."""
+    host, dev = pool
+    g1, s1, a1 = synth.serving_requests([h[0] for h in host], 60, 1e6, seed=51)     # a burst at t ~ 0
+    g2, s2, a2 = synth.serving_requests([h[0] for h in host], 6, 20.0, seed=52)     # sparse, after 0.25 s
+    gid, src = np.concatenate([g1, g2]), np.concatenate([s1, s2])
+    arr = np.concatenate([a1, 0.25 + a2])
+    outs = _outs(host, gid)
+    r = gq.gq_serve(kind, dev, gid, src, arr, mode="adaptive", slots=4, cluster_blocks=2, outs=outs,
+                    switch_backlog=2)
+    assert (r["latency_s"] >= 0).all()
+    assert 0 < r["persistent_requests"] < len(gid)          # both engines served requests
     for o, w in zip(outs, _expected(host, gid, src)):
         assert (o.cpu().numpy().view(np.uint32) == w).all()
 

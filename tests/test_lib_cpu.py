@@ -106,7 +106,7 @@ def _serve_cfg(**kw):
 
 
 @pytest.mark.parametrize("change", [
-    {"kind": 7}, {"mode": 2}, {"cluster_blocks": 3}, {"cluster_blocks": 32}, {"req_graph": [0, 2, 0]}, {"req_src": [3, 50, 99]},
+    {"kind": 7}, {"mode": 3}, {"cluster_blocks": 3}, {"cluster_blocks": 32}, {"req_graph": [0, 2, 0]}, {"req_src": [3, 50, 99]},
     {"arrival": [0.0, 0.2, 0.1]}, {"arrival": [0.0, float("nan"), 0.2]}, {"budget": 0}, {"wait": -1.0},
     {"ngraphs": 0},
 ])
