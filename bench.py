@@ -16,6 +16,7 @@ Also reported:
                dequeue batch, device -> host copy of the results)
   cpu_baseline the oracle's mutex-guarded std::deque on the host cores
   sweep        kernel-only Mops/s per queue for 2^10 .. 2^20 threads
+  phases       enqueue-only then dequeue-only phases (min(2^20, T x ops) items)
 
 --impl reference times the oracle's mutex deque (the CPU reference arm).
 Multi-GPU: independent replicas, one per rank, no collective on the data path.
@@ -532,6 +533,34 @@ def main():
                 cn = cc.cpu().numpy()
                 sweep[k][str(Ts)] = round((cn[0] + cn[2]) / (e0.elapsed_time(e1) * 1e-3) / 1e6, 1)
 
+    # ---- enqueue-only then dequeue-only phases (kernel only, untimed region) ----
+    # every thread enqueues its share of min(2^20, T * ops) items, then (second
+    # launch) every thread dequeues the same number
+    phases = {}
+    if not args.no_sweep:
+        for k in kinds:
+            phases[k] = {}
+            for Ts in sorted({1 << 16, T}):
+                target = min(CAPACITY, Ts * K)
+                cc = torch.zeros(8, dtype=torch.int64, device=dev)
+                res = {}
+                for rep in range(2):
+                    queues[k].reset()
+                    cc.zero_()
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                    ev[0].record()
+                    gq.gq_run(queues[k].handle, gq.GQ_RUN_SPLIT, Ts, producers=Ts, total_ops=target, counts=cc)
+                    ev[1].record()
+                    gq.gq_run(queues[k].handle, gq.GQ_RUN_SPLIT, Ts, producers=0, total_ops=target, counts=cc)
+                    ev[2].record()
+                    ev[2].synchronize()
+                    cn = cc.cpu().numpy()
+                    assert cn[gq.GQ_CNT_ENQ_OK] == target and cn[gq.GQ_CNT_DEQ_OK] == target, (k, Ts, cn)
+                    res = {"items": target,
+                           "enqueue_mops": round(target / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e6, 1),
+                           "dequeue_mops": round(target / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e6, 1)}
+                phases[k][str(Ts)] = res
+
     # ---- end to end through the public batch API with host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -601,7 +630,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between timed steps (256 MiB write); queue state re-initialised inside "
                                  "each step"},
-                "roofline": roofline, "peaks": peaks, "per_queue": per_queue, "sweep": sweep,
+                "roofline": roofline, "peaks": peaks, "per_queue": per_queue, "sweep": sweep, "phases": phases,
                 "cpu_baseline": cpu, "e2e": e2e, "apps": apps, "batched": batched, "serving": serving,
                 "gpu_launches": args.steps * sum(launches_per_step[k] for k in kinds),
                 "clocks": clocks}

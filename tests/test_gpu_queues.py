@@ -8,7 +8,8 @@ results with the oracle, which shares no code with it:
     capacity 2^10, 32-bit tokens): zero EMPTY, zero FULL, exactly once,
     per-producer order;
   * the 50/50 interleaved workload up to 2^20 threads x 100 ops at capacity
-    2^20 and the imbalanced producer/consumer workload (2^18 threads, 10^7 ops,
+    2^20, its enqueue-only-then-dequeue-only phase form, and the imbalanced
+    producer/consumer workload (2^18 threads, 10^7 ops,
     capacity 2^16) with the run-log invariant checks;
   * linearizability of tiny recorded histories (Wing & Gong);
   * the host batch API (exactly once through gq_enqueue_batch/gq_dequeue_batch).
@@ -159,6 +160,29 @@ def test_split_producer_consumer(kind, frac):
         assert rep["enq_full"] > 0          # the bounded queue filled up
     if frac == 0.1:
         assert rep["deq_empty"] > 0
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("T", [1 << 10, 1 << 14, 1 << 20])
+def test_enqueue_then_dequeue_phases(kind, T):
+    """The sweep workload's phase form: every thread enqueues its share of
+    min(2^20, 100 T) items, then (a second launch) every thread dequeues the same
+    number.  All succeed, the queue ends empty, and the concatenated log passes the
+    exactly-once and per-producer-order checks."""
+    cap = 1 << 20
+    target = min(cap, 100 * T)
+    qc, _ = qcap(kind, cap, pool=1 << 22)
+    q = make_queue(kind, qc, 8, max_threads=T)
+    a = run_log(q, gq.GQ_RUN_SPLIT, T, producers=T, total_ops=target)
+    b = run_log(q, gq.GQ_RUN_SPLIT, T, producers=0, total_ops=target)
+    assert a["counts"][gq.GQ_CNT_ENQ_OK] == target and a["counts"][gq.GQ_CNT_ENQ_FULL] == 0
+    assert b["counts"][gq.GQ_CNT_DEQ_OK] == target and b["counts"][gq.GQ_CNT_DEQ_EMPTY] == 0
+    left = drain(q, 16)
+    assert len(left) == 0
+    rep = oracle.check_log(np.concatenate([a["kind"], b["kind"]]), np.concatenate([a["status"], b["status"]]),
+                           np.concatenate([a["val"], b["val"]]), left)
+    assert rep["violations"] == 0, str(rep)
+    assert rep["enq_ok"] == rep["deq_ok"] == target
 
 
 @pytest.mark.parametrize("kind", KINDS)
