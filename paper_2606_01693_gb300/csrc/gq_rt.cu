@@ -131,7 +131,7 @@ template <int KIND>
 __global__ void __launch_bounds__(256) k_rt_trace(const __grid_constant__ RtK k) {
     extern __shared__ float4 sph[];
     for (u32 i = threadIdx.x; i < k.nspheres; i += blockDim.x)
-        sph[i] = make_float4(k.centre[3 * i], k.centre[3 * i + 1], k.centre[3 * i + 2], k.radius[i]);
+        sph[i] = make_float4(k.centre[3 * i], k.centre[3 * i + 1], k.centre[3 * i + 2], k.radius[i] * k.radius[i]);
     __syncthreads();
     const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
     const u32 lane = threadIdx.x & 31;
@@ -171,11 +171,13 @@ __global__ void __launch_bounds__(256) k_rt_trace(const __grid_constant__ RtK k)
             const u32 bounce = bnc[p];
             float best = __int_as_float(0x7f800000);   // +infinity
             int hit = -1;
+            // sph[s].w holds r * r (the same fp32 product the test would form)
+#pragma unroll 4
             for (u32 s = 0; s < k.nspheres; ++s) {
                 const float4 c = sph[s];
                 const float ocx = ox - c.x, ocy = oy - c.y, ocz = oz - c.z;
                 const float b = rt_dot(ocx, ocy, ocz, dx, dy, dz);
-                const float cc = rt_dot(ocx, ocy, ocz, ocx, ocy, ocz) - c.w * c.w;
+                const float cc = rt_dot(ocx, ocy, ocz, ocx, ocy, ocz) - c.w;
                 const float disc = b * b - cc;
                 if (disc < 0.0f) continue;
                 const float sq = sqrtf(disc);
@@ -201,7 +203,8 @@ __global__ void __launch_bounds__(256) k_rt_trace(const __grid_constant__ RtK k)
             } else {
                 const float4 c = sph[hit];
                 const float hx = ox + best * dx, hy = oy + best * dy, hz = oz + best * dz;
-                const float nx = (hx - c.x) / c.w, ny = (hy - c.y) / c.w, nz = (hz - c.z) / c.w;
+                const float rad = k.radius[hit];     // sph[].w holds the squared radius
+                const float nx = (hx - c.x) / rad, ny = (hy - c.y) / rad, nz = (hz - c.z) / rad;
                 tr = tr * k.albedo[3 * hit];
                 tg = tg * k.albedo[3 * hit + 1];
                 tb = tb * k.albedo[3 * hit + 2];
