@@ -158,3 +158,23 @@ def test_device_wait_limit_reports_timeout(pool):
     assert ei.value.status == gq.GQ_ERR_TIMEOUT
     r = gq.gq_serve("lfq", dev, [0], [0], [0.0], mode="persistent", slots=1, cluster_blocks=1)
     assert r["latency_s"][0] >= 0
+
+
+@pytest.mark.parametrize("mode", ["persistent", "adaptive"])
+def test_full_size_pool_sampled(mode):
+    """The serving workload's shape: R-MAT graphs of scales 10..20 (both ends present),
+    Poisson arrivals at 10,000 req/s, 8-block clusters, 32 GiB budget; the distances
+    of a sample of requests (the largest graphs among them) equal the oracle's."""
+    scales = np.concatenate([[10, 20], synth.rmat_pool_scales(10, 10, 20, 2026)])
+    host = [synth.rmat_csr_fast(int(s), seed=7000 + i) for i, s in enumerate(scales)]
+    dev = [(torch.from_numpy(o.view(np.int64)).cuda(), torch.from_numpy(a.view(np.int32)).cuda()) for o, a in host]
+    gid, src, arr = synth.serving_requests([h[0] for h in host], 400, 10000.0, seed=99)
+    order = np.argsort(-scales[gid], kind="stable")
+    sample = set(order[:6].tolist()) | set(range(0, 400, 67))
+    outs = [torch.empty(len(host[g][0]) - 1, dtype=torch.int32, device="cuda") if i in sample else None
+            for i, g in enumerate(gid)]
+    r = gq.gq_serve("lfq", dev, gid, src, arr, mode=mode, cluster_blocks=8, budget_bytes=32 << 30, outs=outs)
+    assert (r["latency_s"] >= 0).all()
+    for i in sorted(sample):
+        want = oracle.bfs(host[gid[i]][0], host[gid[i]][1], int(src[i]))
+        assert (outs[i].cpu().numpy().view(np.uint32) == want).all(), i
