@@ -107,6 +107,18 @@ int gq_atomic_peak(int pattern, uint32_t blocks, uint32_t threads, uint32_t iter
                    unsigned long long* d_buf, uint64_t buf_words, unsigned long long* d_sink,
                    void* stream);
 
+/* WaveFAA probe (Algorithm 1 WaveFAA; Lemma "WaveFAA preserves ticket order").
+ * Thread t of a grid of `threads` threads (blocks of 256) takes one ticket if
+ * d_take[t] is non-zero: lanes with d_take[t] == 1 on counter d_counters[0],
+ * lanes with 2 on d_counters[1] (lanes of one warp may mix both: they are
+ * grouped by counter address), with batch width `width` (1 .. 32, a power of
+ * two).  The ticket goes to d_tickets[t] (others get ~0).  Test hook: the
+ * tickets of each counter must be exactly 0 .. count-1, and within a warp's
+ * group of `width` lanes the lanes that share a counter get consecutive tickets
+ * in lane order.  Errors: GQ_ERR_INVALID, GQ_ERR_CUDA. */
+int gq_wavefaa_probe(const uint8_t* d_take, uint32_t threads, uint32_t width, unsigned long long* d_counters,
+                     unsigned long long* d_tickets, void* stream);
+
 /* ---- many independent queues in one persistent launch (batched form) ----
  *
  * gq_multi_prepare copies the device views of Q queues (same kind and element

@@ -38,7 +38,7 @@ EXPORTS = [
     "gq_sync_status", "gq_device_view", "gq_info", "gq_status_str", "gq_get_stats",
     "gq_run", "gq_run_sequence", "gq_drain", "gq_atomic_peak", "gq_fifo_static_roundtrip",
     "gq_bfs", "gq_render_workspace_bytes", "gq_render", "gq_multi_prepare", "gq_run_multi",
-    "gq_bfs_batch_workspace_bytes", "gq_bfs_batch", "gq_serve",
+    "gq_bfs_batch_workspace_bytes", "gq_bfs_batch", "gq_serve", "gq_wavefaa_probe",
 ]
 GQ_VIEW_BYTES = 512
 
@@ -105,6 +105,7 @@ def load() -> ctypes.CDLL:
         "gq_bfs_batch_workspace_bytes": [u32, P],
         "gq_bfs_batch": [P, P, u32, u32, P, P, u32, P, P, P],
         "gq_serve": [P, P],
+        "gq_wavefaa_probe": [P, u32, u32, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -221,6 +222,12 @@ def gq_drain(h: int, out, count, max_items: int | None = None, stream=None) -> N
 def gq_atomic_peak(pattern: int, blocks: int, threads: int, iters: int, buf, sink, stream=None) -> None:
     _check(load().gq_atomic_peak(pattern, blocks, threads, iters, _ptr(buf), buf.numel(), _ptr(sink),
                                  _stream(stream)), "gq_atomic_peak")
+
+
+def gq_wavefaa_probe(take, width: int, counters, tickets, stream=None) -> None:
+    """Test hook for WaveFAA: thread t takes a ticket on counter take[t]-1 (1 or 2), batch width `width`."""
+    _check(load().gq_wavefaa_probe(_ptr(take), take.numel(), width, _ptr(counters), _ptr(tickets), _stream(stream)),
+           "gq_wavefaa_probe")
 
 
 def gq_fifo_static_roundtrip(items, out, num_out, n: int | None = None, stream=None) -> None:

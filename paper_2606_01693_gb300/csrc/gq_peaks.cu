@@ -78,7 +78,24 @@ __global__ void k_peak(int pattern, u32 iters, u64* buf, u64 words, unsigned lon
     if (acc == 0x5EEDull) atomicAdd(sink, 1ull);
 }
 
+__global__ void k_wavefaa_probe(const uint8_t* take, u32 threads, u32 width, u64* counters, u64* tickets) {
+    const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= threads) return;
+    u64 ticket = ~0ull;
+    if (take[t] == 1 || take[t] == 2) ticket = warp_faa<true>(counters + (take[t] - 1), 1, width);
+    tickets[t] = ticket;
+}
+
 }  // namespace
+
+extern "C" int gq_wavefaa_probe(const uint8_t* d_take, uint32_t threads, uint32_t width, unsigned long long* d_counters,
+                                unsigned long long* d_tickets, void* stream) {
+    if (!d_take || !threads || !d_counters || !d_tickets || width == 0 || width > 32 || (width & (width - 1)))
+        return GQ_ERR_INVALID;
+    k_wavefaa_probe<<<(threads + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        d_take, threads, width, reinterpret_cast<u64*>(d_counters), reinterpret_cast<u64*>(d_tickets));
+    return gq_check_launch();
+}
 
 extern "C" int gq_atomic_peak(int pattern, uint32_t blocks, uint32_t threads, uint32_t iters,
                               unsigned long long* d_buf, uint64_t buf_words, unsigned long long* d_sink,

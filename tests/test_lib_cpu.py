@@ -125,3 +125,12 @@ def test_atomic_peak_arguments_validated():
     assert L.gq_atomic_peak(gq.GQ_PEAK_SPREAD_FAA, 1, 32, 1, buf, 16 * 512 - 1, sink, None) == gq.GQ_ERR_INVALID
     assert L.gq_atomic_peak(gq.GQ_PEAK_PACKED_FAA, 1, 32, 1, buf, 16 * 16 - 1, sink, None) == gq.GQ_ERR_INVALID
     assert L.gq_atomic_peak(gq.GQ_PEAK_SAME_ADDR_FAA, 1, 33, 1, buf, 64, sink, None) == gq.GQ_ERR_INVALID
+
+
+def test_wavefaa_probe_arguments_validated():
+    L = gq.load()
+    p = ctypes.c_void_p(0x1000)   # never dereferenced: every call below fails validation first
+    for width in (0, 3, 64):
+        assert L.gq_wavefaa_probe(p, 64, width, p, p, None) == gq.GQ_ERR_INVALID
+    assert L.gq_wavefaa_probe(p, 0, 32, p, p, None) == gq.GQ_ERR_INVALID
+    assert L.gq_wavefaa_probe(None, 64, 32, p, p, None) == gq.GQ_ERR_INVALID
