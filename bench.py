@@ -59,7 +59,8 @@ def parse():
     p.add_argument("--no-sweep", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-threads", type=int, default=1 << 17, help="logical threads in the CPU sample")
+    p.add_argument("--cpu-threads", type=int, default=1 << 19,
+                   help="logical threads in the CPU sample (2^19 x 100 ops: about 10 s on the 16 host cores)")
     p.add_argument("--no-apps", action="store_true", help="skip the application measurements (BFS, ray tracing)")
     p.add_argument("--no-batched", action="store_true", help="skip the batched / persistent / graph comparisons")
     p.add_argument("--no-serving", action="store_true", help="skip the BFS serving measurements")
