@@ -49,7 +49,7 @@ NCU_TRAFFIC = {"lfq": 46699776 + 13850368, "wfq": 63783680 + 206591232, "ymc": 9
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--threads", type=int, default=1 << 20)
@@ -91,7 +91,7 @@ def dist_env():
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -99,12 +99,14 @@ class Clocks:
         self.p = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(device_index)],
+                                       "-lms", "100", "-i", str(device_index)],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
 
-    def stop(self):
+    def stop(self, window=None):
+        """Median SM clock and throttle reasons of the samples taken inside
+        `window` (host epoch seconds, start and end of the timed region)."""
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
@@ -113,22 +115,24 @@ class Clocks:
         except Exception:
             self.p.kill()
             out = ""
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+        rows = []
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        inside = [r for r in rows if window and window[0] <= r[0] <= window[1]]
+        use = inside or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = {nm for r in use for nm, v in zip(names, r[3]) if v.lower().startswith("active")}
+        sm = [r[1] for r in use]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "samples": len(sm), "samples_in_timed_region": len(inside), "reasons": sorted(reasons)}
 
 
 def cpu_baseline(T, K, seed, cpu_threads):
@@ -354,7 +358,10 @@ def run_reference(args):
     import oracle
     import synth
     T, K = args.threads, args.ops
-    Ts = min(T, args.cpu_threads)
+    # every step a bounded sample: the --cpu-threads budget shared by all steps
+    # (warm-up included), so the whole run takes about as long as one CPU baseline
+    per_step = max(1 << 12, args.cpu_threads // max(1, args.steps + args.warmup))
+    Ts = min(T, 1 << (per_step.bit_length() - 1))
     sched = synth.mixed_schedule_bits(args.seed, Ts, K)
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
@@ -450,6 +457,7 @@ def main():
             if evs is not None:
                 evs[k][1].record()
 
+    clk = Clocks(local)                      # started before the warm-up: sampling by the timed region
     for _ in range(args.warmup):
         step()
     for k in kinds:
@@ -458,7 +466,7 @@ def main():
             raise SystemExit("device error in warm-up: %s" % gq.status_str(st))
         counts[k].zero_()
     barrier()
-    clk = Clocks(local)
+    t_region = time.time()
     step_ms, kern_ms = [], {k: 0.0 for k in kinds}
     for _ in range(args.steps):
         flush.fill_(1)                       # L2 flush between timed steps (256 MiB write)
@@ -472,7 +480,7 @@ def main():
         for k in kinds:
             kern_ms[k] += evs[k][0].elapsed_time(evs[k][1])
     barrier()
-    clocks = clk.stop()
+    clocks = clk.stop(window=(t_region, time.time()))
     for k in kinds:
         st = queues[k].sync_status()
         if st != 0:
