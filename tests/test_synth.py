@@ -66,3 +66,27 @@ def test_grid_neighbours_sorted_and_symmetric():
         nb = adj[off[v]:off[v + 1]]
         assert (np.diff(nb.astype(np.int64)) > 0).all()
     assert set(zip(src.tolist(), adj.tolist())) == set(zip(adj.tolist(), src.tolist()))
+
+
+def test_pool_scales_cover_range_uniformly():
+    s = synth.rmat_pool_scales(11000, 10, 20, 7)
+    assert s.min() == 10 and s.max() == 20
+    counts = np.bincount(s - 10, minlength=11)
+    assert (np.abs(counts - 1000) < 150).all()          # uniform integer scales, ~1000 each
+    assert (synth.rmat_pool_scales(50, 10, 20, 7) == s[:50]).all()   # deterministic by seed
+
+
+def test_serving_requests_poisson_and_valid_sources():
+    offs = [synth.grid_csr(5, 4)[0], synth.rmat_csr(8, seed=3)[0]]
+    gid, src, arr = synth.serving_requests(offs, 20000, 1000.0, seed=11)
+    assert arr[0] == 0.0 and (np.diff(arr) >= 0).all()
+    gaps = np.diff(arr)
+    assert abs(gaps.mean() - 1e-3) < 0.05e-3              # exponential gaps, mean 1 / rate
+    assert abs(np.median(gaps) - np.log(2) * 1e-3) < 0.05e-3   # exponential median ln2 / rate
+    assert set(np.unique(gid).tolist()) == {0, 1}
+    for g, v in zip(gid[:500], src[:500]):
+        off = offs[g]
+        assert v < len(off) - 1
+        assert off[v + 1] > off[v]                        # a non-isolated source
+    g2, s2, a2 = synth.serving_requests(offs, 20000, 1000.0, seed=11)
+    assert (g2 == gid).all() and (s2 == src).all() and (a2 == arr).all()
