@@ -291,7 +291,7 @@ def bench_batched(gq, synth, kinds, dev, reps=3):
             mq.run(TPQ, PPQ, OPQ, counts, blocks=best["blocks"])
         t = _timed(g2.replay, reps)
         res["tuned_graph_mops"] = round(succ() / (t * 1e-3) / 1e6, 1)
-        res["tuned"] = {kk: best[kk] for kk in ("batch_width", "blocks", "backoff_ns", "patience")}
+        res["tuned"] = {kk: best[kk] for kk in ("batch_width", "blocks", "backoff_ns", "patience", "help_delay")}
         out["queues256_%s" % k] = res
         mq.close()
     # batched BFS

@@ -124,8 +124,10 @@ int gq_wavefaa_probe(const uint8_t* d_take, uint32_t threads, uint32_t width, un
  * gq_multi_prepare copies the device views of Q queues (same kind and element
  * size) into d_views (Q * sizeof(gq_dev) bytes of device memory; sizeof(gq_dev)
  * never exceeds GQ_VIEW_BYTES).  `tune` (nullable) overrides, in every copied
- * view, the WaveFAA batch width (if non-zero), the back-off, and, when
- * tune->patience_set is 1, G-WFQ's patience; this is how the autotuner tries
+ * view, the WaveFAA batch width (if non-zero), the back-off, when
+ * tune->patience_set is 1 G-WFQ's patience, and when tune->help_delay is
+ * non-zero G-WFQ's help delay D (GQ_ERR_TOO_MANY_THREADS if some queue would
+ * leave its cycle-tag bound R > D k / n + 6); this is how the autotuner tries
  * settings without recreating queues.  Asynchronous on `stream`. */
 int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void* d_views, const gq_options* tune,
                      void* stream);

@@ -327,10 +327,11 @@ class MultiQueue:
         self.views = torch.empty(len(self.queues) * GQ_VIEW_BYTES, dtype=torch.uint8, device="cuda")
         self.prepare()
 
-    def prepare(self, batch_width: int = 0, backoff_ns: int | None = None, patience=None, stream=None):
+    def prepare(self, batch_width: int = 0, backoff_ns: int | None = None, patience=None, help_delay: int = 0,
+                stream=None):
         tune = None
-        if batch_width or backoff_ns is not None or patience is not None:
-            tune = gq_options(batch_width=batch_width, backoff_ns=backoff_ns or 0)
+        if batch_width or backoff_ns is not None or patience is not None or help_delay:
+            tune = gq_options(batch_width=batch_width, backoff_ns=backoff_ns or 0, help_delay=help_delay)
             if patience is not None:
                 tune.patience_enq, tune.patience_deq, tune.patience_set = patience[0], patience[1], 1
         gq_multi_prepare(self.handles, self.views, tune, stream)

@@ -39,28 +39,38 @@ def _save_cache(c: dict) -> None:
 
 def tune_multi(mq, threads_per_queue: int, producers_per_queue: int, ops_per_queue: int,
                widths=(32, 16, 8, 4, 1), blocks_per_sm=(0, 2, 4, 8), backoffs=(0, 100, 400), reps: int = 3,
-               use_cache: bool = True, block: int = 256, patiences=None) -> dict:
-    """Returns {"batch_width", "blocks", "backoff_ns", "patience", "mops", "table"} for
-    MultiQueue `mq` and leaves `mq` prepared with the winning settings.  G-WFQ
+               use_cache: bool = True, block: int = 256, patiences=None, help_delays=None) -> dict:
+    """Returns {"batch_width", "blocks", "backoff_ns", "patience", "help_delay", "mops", "table"}
+    for MultiQueue `mq` and leaves `mq` prepared with the winning settings.  G-WFQ
     queues also try the patience pairs (enqueue, dequeue) in `patiences`
-    (default (16, 64), (64, 256), (256, 1024))."""
+    (default (16, 64), (64, 256), (256, 1024)) and the help delays D in
+    `help_delays` (default 0 = keep the queues' own, 16 and 256; a D that breaks
+    some queue's cycle-tag bound is skipped)."""
     if patiences is None:
         patiences = [(16, 64), (64, 256), (256, 1024)] if mq.kind == 1 else [None]
+    if help_delays is None:
+        help_delays = [0, 16, 256] if mq.kind == 1 else [0]
     import torch
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    key = "%s|kind%d|q%d|tpq%d|ppq%d|opq%d|cap%d" % (props.name, mq.kind, len(mq.queues), threads_per_queue,
+    key = "v2|%s|kind%d|q%d|tpq%d|ppq%d|opq%d|cap%d" % (props.name, mq.kind, len(mq.queues), threads_per_queue,
                                                      producers_per_queue, ops_per_queue,
                                                      int(sum(q.capacity for q in mq.queues)))
     cache = _load_cache() if use_cache else {}
     if use_cache and key in cache:
         best = cache[key]
         pat = tuple(best["patience"]) if best.get("patience") else None
-        mq.prepare(batch_width=best["batch_width"], backoff_ns=best["backoff_ns"], patience=pat)
+        mq.prepare(batch_width=best["batch_width"], backoff_ns=best["backoff_ns"], patience=pat,
+                   help_delay=best.get("help_delay", 0))
         return dict(best, cached=True)
     counts = torch.zeros(8, dtype=torch.int64, device="cuda")
     table = []
-    for w, bo, pat in [(w, bo, pat) for w in widths for bo in backoffs for pat in patiences]:
-        mq.prepare(batch_width=w, backoff_ns=bo, patience=pat)
+    from . import GqError
+    for w, bo, pat, dl in [(w, bo, pat, dl) for w in widths for bo in backoffs for pat in patiences
+                           for dl in help_delays]:
+        try:
+            mq.prepare(batch_width=w, backoff_ns=bo, patience=pat, help_delay=dl)
+        except GqError:
+            continue                       # D outside some queue's cycle-tag bound
         for bps in blocks_per_sm:
             blocks = bps * props.multi_processor_count
             ms = []
@@ -77,10 +87,11 @@ def tune_multi(mq, threads_per_queue: int, producers_per_queue: int, ops_per_que
             c = counts.cpu().numpy()
             mops = float(c[0] + c[2]) / (float(np.median(ms)) * 1e-3) / 1e6
             table.append({"batch_width": w, "backoff_ns": bo, "blocks": blocks, "patience": pat,
-                          "mops": round(mops, 1)})
+                          "help_delay": dl, "mops": round(mops, 1)})
     best = max(table, key=lambda r: r["mops"])
     pat = tuple(best["patience"]) if best.get("patience") else None
-    mq.prepare(batch_width=best["batch_width"], backoff_ns=best["backoff_ns"], patience=pat)
+    mq.prepare(batch_width=best["batch_width"], backoff_ns=best["backoff_ns"], patience=pat,
+               help_delay=best["help_delay"])
     out = dict(best)
     if use_cache:
         cache[key] = out

@@ -241,7 +241,8 @@ int launch_multi(const gq_dev* views, const gq_multi_args& g, cudaStream_t st) {
     return gq_check_launch();
 }
 
-__global__ void k_multi_tune(gq_dev* views, u32 n, u32 width, u32 backoff, u32 set_patience, u32 pe, u32 pd) {
+__global__ void k_multi_tune(gq_dev* views, u32 n, u32 width, u32 backoff, u32 set_patience, u32 pe, u32 pd,
+                             u32 delay) {
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (width) views[i].batch_width = width;
@@ -250,6 +251,7 @@ __global__ void k_multi_tune(gq_dev* views, u32 n, u32 width, u32 backoff, u32 s
         views[i].patience_enq = pe;
         views[i].patience_deq = pd;
     }
+    if (delay && views[i].kind == GQ_WFQ) views[i].help_delay = delay;
 }
 
 }  // namespace
@@ -263,6 +265,14 @@ extern "C" int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void*
             return GQ_ERR_INVALID;
     if (tune && tune->batch_width && (tune->batch_width > 32 || (tune->batch_width & (tune->batch_width - 1))))
         return GQ_ERR_INVALID;
+    // a new G-WFQ help delay D must keep every queue within its modular-cycle bound R > D k / n + 6
+    if (tune && tune->help_delay && queues[0]->dev.kind == GQ_WFQ)
+        for (uint32_t i = 0; i < nqueues; ++i) {
+            const gq_dev& d = queues[i]->dev;
+            const double R = (double)(1ull << d.cycle_bits);
+            if (!(R > (double)tune->help_delay * (double)d.max_threads / (double)d.capacity + 6.0))
+                return GQ_ERR_TOO_MANY_THREADS;
+        }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     gq_dev* v = static_cast<gq_dev*>(d_views);
     for (uint32_t i = 0; i < nqueues; ++i)
@@ -270,7 +280,8 @@ extern "C" int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void*
             return GQ_ERR_CUDA;
     if (tune) {
         k_multi_tune<<<(nqueues + 255) / 256, 256, 0, st>>>(v, nqueues, tune->batch_width, tune->backoff_ns,
-                                                            tune->patience_set, tune->patience_enq, tune->patience_deq);
+                                                            tune->patience_set, tune->patience_enq, tune->patience_deq,
+                                                            tune->help_delay);
         return gq_check_launch();
     }
     return GQ_OK;

@@ -98,3 +98,25 @@ def test_autotuner_picks_a_valid_setting(tmp_path, monkeypatch):
     mq.run(TPQ, PPQ, OPQ, counts, blocks=best["blocks"])
     _check(mq, counts, Q, TPQ, PPQ, OPQ)
     mq.close()
+
+
+def test_wfq_help_delay_tuning_and_bound(tmp_path, monkeypatch):
+    """The G-WFQ help delay D is a tuned knob; a D that would break some queue's
+    cycle-tag bound R > D k / n + 6 is refused and skipped by the autotuner, and
+    the tuned setting still passes the run checks."""
+    monkeypatch.setenv("GQ_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
+    Q, TPQ, OPQ, PPQ = 8, 256, 4000, 128
+    mq = gq.MultiQueue("wfq", _caps("wfq", Q, 5, OPQ), 8, TPQ)
+    R = 1 << 19
+    too_big = (R - 6) * min(q.capacity for q in mq.queues) // TPQ + 1
+    with pytest.raises(gq.GqError) as ei:
+        mq.prepare(help_delay=too_big)
+    assert ei.value.status == gq.GQ_ERR_TOO_MANY_THREADS
+    best = autotune.tune_multi(mq, TPQ, PPQ, OPQ, widths=(32,), blocks_per_sm=(0,), backoffs=(0,), reps=1,
+                               patiences=[(16, 64)], help_delays=[0, 1, too_big])
+    assert {r["help_delay"] for r in best["table"]} == {0, 1}
+    counts = torch.zeros(8, dtype=torch.int64, device=DEV)
+    mq.reset()
+    mq.run(TPQ, PPQ, OPQ, counts, blocks=best["blocks"])
+    _check(mq, counts, Q, TPQ, PPQ, OPQ)
+    mq.close()
