@@ -43,7 +43,7 @@ CAPACITY = 1 << 20
 # capture of `bench.py --steps 1 --warmup 3 --no-sweep --no-e2e --no-cpu --no-apps --no-batched
 # --no-serving` with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass; profiles/).
 # Set to None whenever the kernels change.
-NCU_TRAFFIC = {"lfq": 46699776 + 13850368, "wfq": 63783680 + 206591232, "ymc": 986322176 + 827432960}
+NCU_TRAFFIC = {"lfq": 46877440 + 11752960, "wfq": 63910400 + 207450624, "ymc": 986393344 + 826461440}
 
 
 def parse():
