@@ -2,6 +2,8 @@
 // Section V-A and the recorders used by the correctness checks of Section IV.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "../../include/gq_drivers.h"
 #include "gq_host.h"
 #include "gq_ops.cuh"
@@ -146,7 +148,32 @@ __global__ void k_drain(const __grid_constant__ gq_dev q, u64* out, u64 max, uns
 template <class T, int KIND>
 int launch_run(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
     const u32 grid = (a.threads + block - 1) / block;
-    k_run<T, KIND><<<grid, block, 0, st>>>(h->dev, a);
+    // G-LFQ on a grid of at least two waves at 768 threads per SM: reserve
+    // (unused) dynamic shared memory so that only 768 threads per SM are
+    // resident.  Fewer threads contend for the Head / Tail / Threshold lines at
+    // once and the ring's CAS retries drop; the blocks beyond the first wave
+    // start as earlier ones finish.  G-WFQ and G-WFQ-YMC run slower with the
+    // cap, and so does a grid that would fit in one uncapped wave.
+    size_t smem = 0;
+    if (KIND == GQ_LFQ) {
+        const u32 per_sm = block >= 768 ? 1u : 768u / block;
+        int sm_bytes = 0, reserved = 0, optin = 0;
+        if ((u64)grid >= 2ull * per_sm * (u64)h->sm_count &&
+            cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device) == cudaSuccess &&
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, h->device) == cudaSuccess &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) == cudaSuccess) {
+            // a block's footprint halfway between sm/(per_sm + 1) and sm/per_sm:
+            // per_sm blocks fit, one more does not
+            const int foot = (sm_bytes / (int)per_sm + sm_bytes / (int)(per_sm + 1)) / 2;
+            smem = (size_t)std::min(std::max(foot - reserved, 0), optin);
+            if (smem && cudaFuncSetAttribute(k_run<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                            cudaSuccess) {
+                cudaGetLastError();
+                smem = 0;
+            }
+        }
+    }
+    k_run<T, KIND><<<grid, block, smem, st>>>(h->dev, a);
     return gq_check_launch();
 }
 
