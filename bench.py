@@ -37,8 +37,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "queue Mops/s (enq+deq) vs threads; % of measured L2-atomic peak; serving p99"
 CAPACITY = 1 << 20
-# DRAM bytes per launch of each run kernel from one ncu capture (profiles/);
-# None until captured for the current kernels.
 # DRAM bytes (read + write) per launch of each run kernel at the headline size, from one ncu
 # capture of `bench.py --steps 1 --warmup 3 --no-sweep --no-e2e --no-cpu --no-apps --no-batched
 # --no-serving` with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass; profiles/).
@@ -236,7 +234,7 @@ def _timed(fn, reps):
     return float(np.median(ms))
 
 
-def bench_batched(gq, synth, kinds, dev, reps=3):
+def bench_batched(gq, synth, kinds, dev, reps=7):
     """Batched forms against the plain per-call form on the same GPU.
     (1) 256 independent queues, capacities log-uniform 2^8 .. 2^16 (seed 0),
         2^18 threads (1024 per queue), 10^7 operations, 50 % producers; one step
@@ -283,7 +281,7 @@ def bench_batched(gq, synth, kinds, dev, reps=3):
         t = _timed(g.replay, reps)
         res["graph_mops"] = round(succ() / (t * 1e-3) / 1e6, 1)
         best = autotune.tune_multi(mq, TPQ, PPQ, OPQ, widths=(32, 16, 8), blocks_per_sm=(0, 4), backoffs=(0, 200),
-                                   reps=2)
+                                   reps=3)
         g2 = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g2):
             counts.zero_()
