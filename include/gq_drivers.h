@@ -12,9 +12,9 @@
  *                     GQ_RUN_SPLIT  "split producer/consumer kernel": the first
  *                                   `producers` threads only enqueue, the rest
  *                                   only dequeue; `total_ops` split evenly.
- *                   Optionally records, per operation, the status, the value and
+ *                   Optionally records, per operation, the status, the value,
  *                   globaltimer timestamps (Section IV: device-recorded histories
- *                   {proc, op, arg, ret, call, end}).
+ *                   {proc, op, arg, ret, call, end}) and the ticket.
  *   gq_run_sequence a single device thread applies an explicit op list (the
  *                   sequential bit-exactness test against the FIFO specification).
  *   gq_drain        a single device thread dequeues until EMPTY (FIFO order of
@@ -69,6 +69,14 @@ typedef struct {
     uint64_t* d_call;         /* nullable, op-major: globaltimer before the op             */
     uint64_t* d_end;          /* nullable, op-major: globaltimer after the op              */
     unsigned long long* d_counts; /* 8 words, added to (the caller zeroes them)           */
+    uint64_t* d_ticket;       /* nullable, op-major, test recorder: a successful op's     */
+                              /* ticket in the allocated-index ring aq (G-LFQ, G-WFQ;     */
+                              /* G-WFQ: the 43-bit Global counter value) or its cell     */
+                              /* (G-WFQ-YMC); 2^64-1 for an op that did not succeed.     */
+                              /* An item's enqueue and the dequeue that returns it have  */
+                              /* the same ticket, and of two enqueues (dequeues) that do */
+                              /* not overlap in time the earlier has the smaller one.    */
+                              /* Non-null selects a separate recording kernel.           */
 } gq_run_args;
 
 /* Launches the driver kernel.  For SPLIT, ops per thread = ceil(total_ops /

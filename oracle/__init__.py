@@ -8,6 +8,7 @@ What it computes (see ``oracle.h`` for the C entry points):
   * ``seqfifo_run``    the sequential FIFO specification (Section IV's queue model)
   * ``linearizable``   Wing & Gong linearizability search for tiny histories
   * ``check_log``      exactly-once / per-producer-order / no-overtaking checks
+  * ``check_tickets``  ticket matching, distinctness and real-time order checks
   * ``mutex_run``      mutex-guarded std::deque on N host threads (timed baseline)
   * ``bfs``            textbook sequential BFS
   * ``render_pixels``  sequential CPU ray tracer (per-pixel radiance)
@@ -56,6 +57,8 @@ def lib():
         L.orc_linearizable.restype = ctypes.c_int
         L.orc_check_log.argtypes = [i64, i64, P, P, P, P, i64, i32, u64, u64, ctypes.POINTER(Report)]
         L.orc_check_log.restype = i64
+        L.orc_check_tickets.argtypes = [i64, P, P, P, P, P, P, i32, ctypes.POINTER(Report)]
+        L.orc_check_tickets.restype = i64
         L.orc_mutex_run.argtypes = [i32, i64, i64, P, i64, P, u64, i32, P]
         L.orc_mutex_run.restype = ctypes.c_double
         L.orc_bfs.argtypes = [i64, P, P, u32, P]
@@ -103,6 +106,24 @@ def check_log(kind, status, val, drained, prod_shift=32, seq_mask=0xFFFFFFFF, se
     rep = Report()
     lib().orc_check_log(T, K, _p(kind), _p(status), _p(val), _p(drained), len(drained),
                         prod_shift, seq_mask, seq_bias, ctypes.byref(rep))
+    return {f: getattr(rep, f) for f, _ in Report._fields_ if f != "pad"}
+
+
+def check_tickets(kind, status, val, ticket, call=None, end=None, bits=64):
+    """Ticket checks (matching, distinct, real-time order) on a run log of any
+    shape; the arrays are flattened alike.  Returns a dict report."""
+    kind = np.ascontiguousarray(kind, dtype=np.uint8).ravel()
+    status = np.ascontiguousarray(status, dtype=np.int8).ravel()
+    val = np.ascontiguousarray(val, dtype=np.uint64).ravel()
+    ticket = np.ascontiguousarray(ticket, dtype=np.uint64).ravel()
+    if call is not None:
+        call = np.ascontiguousarray(call, dtype=np.uint64).ravel()
+        end = np.ascontiguousarray(end, dtype=np.uint64).ravel()
+    rep = Report()
+    r = lib().orc_check_tickets(len(kind), _p(kind), _p(status), _p(val), _p(ticket), _p(call), _p(end), bits,
+                                ctypes.byref(rep))
+    if r < 0:
+        raise ValueError("orc_check_tickets: bad arguments")
     return {f: getattr(rep, f) for f, _ in Report._fields_ if f != "pad"}
 
 

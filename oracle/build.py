@@ -9,7 +9,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["fifo.cpp", "linearize.cpp", "check.cpp", "bfs.cpp", "rt.cpp"]
+SOURCES = ["fifo.cpp", "linearize.cpp", "check.cpp", "tickets.cpp", "bfs.cpp", "rt.cpp"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -19,6 +19,8 @@
  *                          (Section IV "Linearizability via Porcupine")
  *   - orc_check_log        exactly-once / no out-of-range token / per-producer
  *                          order checks (Section IV "Device-side FIFO conformance")
+ *   - orc_check_tickets    ticket checks: an item's dequeue has its enqueue's
+ *                          ticket, tickets are distinct and follow real time
  *   - orc_mutex_run        a mutex-guarded std::deque running the same seeded
  *                          schedule on N host threads (the timed CPU baseline)
  *   - orc_bfs              textbook sequential breadth-first search (Section V-B
@@ -62,7 +64,12 @@ typedef struct {
     int32_t first_kind;      /* 0 none, 1 multiset mismatch, 2 per-consumer order,
                                 3 overtaking (a drained token older than a dequeued one
                                 of the same producer), 4 drained order, 5 bad token,
-                                6 bad status */
+                                6 bad status; orc_check_tickets: 7 a ticket
+                                wider than `bits`, 8 a dequeue's ticket differs from
+                                its value's enqueue ticket (or the value was never
+                                enqueued), 9 two enqueues (dequeues) share a ticket,
+                                10 enqueue tickets against real-time order,
+                                11 dequeue tickets against real-time order */
     int32_t pad;
     int64_t first_index;     /* flat index (i * T + t) or drained index of the first violation */
 } orc_report;
@@ -78,6 +85,19 @@ typedef struct {
 int64_t orc_check_log(int64_t T, int64_t K, const uint8_t* kind, const int8_t* status,
                       const uint64_t* val, const uint64_t* drained, int64_t n_drained,
                       int32_t prod_shift, uint64_t seq_mask, uint64_t seq_bias, orc_report* rep);
+
+/* Ticket checks on a run log of n operations (flat, any order): kind 1
+ * enqueue / 0 dequeue / other none, status 0 = OK, val the token, ticket the
+ * recorded ticket of a successful op (a `bits`-bit counter value, may wrap),
+ * call / end (both nullable) globaltimer stamps.  Checks that every dequeue's
+ * ticket equals its value's enqueue ticket, that no two enqueues (dequeues)
+ * share one, and, with stamps, that an operation has a larger ticket than
+ * every operation of its kind that ended before it was called.  rep counts
+ * enq_ok / deq_ok and the violations.  Returns the number of violations, -1
+ * on bad arguments. */
+int64_t orc_check_tickets(int64_t n, const uint8_t* kind, const int8_t* status, const uint64_t* val,
+                          const uint64_t* ticket, const uint64_t* call, const uint64_t* end, int32_t bits,
+                          orc_report* rep);
 
 /* Mutex-guarded std::deque running a workload on `nthreads` host threads; host
  * thread h runs logical threads t = h, h + nthreads, ...

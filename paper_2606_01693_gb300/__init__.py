@@ -62,7 +62,7 @@ class gq_run_args(ctypes.Structure):
                 ("ops", ctypes.c_uint32), ("producers", ctypes.c_uint32), ("delay_ns", ctypes.c_uint32),
                 ("total_ops", ctypes.c_uint64), ("d_sched", ctypes.c_void_p), ("d_status", ctypes.c_void_p),
                 ("d_val", ctypes.c_void_p), ("d_call", ctypes.c_void_p), ("d_end", ctypes.c_void_p),
-                ("d_counts", ctypes.c_void_p)]
+                ("d_counts", ctypes.c_void_p), ("d_ticket", ctypes.c_void_p)]
 
 
 _lib = None
@@ -203,9 +203,9 @@ def gq_info(h: int) -> tuple[int, bool]:
 
 def gq_run(h: int, mode: int, threads: int, block: int = 256, ops: int = 0, producers: int = 0,
            total_ops: int = 0, sched=None, status=None, val=None, call=None, end=None, counts=None,
-           delay_ns: int = 0, stream=None) -> None:
+           delay_ns: int = 0, stream=None, ticket=None) -> None:
     a = gq_run_args(mode, threads, block, ops, producers, delay_ns, total_ops, _ptr(sched), _ptr(status),
-                    _ptr(val), _ptr(call), _ptr(end), _ptr(counts))
+                    _ptr(val), _ptr(call), _ptr(end), _ptr(counts), _ptr(ticket))
     _check(load().gq_run(h, ctypes.byref(a), _stream(stream)), "gq_run")
 
 

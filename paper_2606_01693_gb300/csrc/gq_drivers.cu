@@ -23,6 +23,7 @@ struct RunK {
     u64* call;
     u64* end;
     unsigned long long* counts;
+    u64* ticket;
 };
 
 __device__ __forceinline__ u32 mix32(u32 a, u32 b) {
@@ -35,7 +36,9 @@ __device__ __forceinline__ u32 mix32(u32 a, u32 b) {
 
 // 256 threads x 4 blocks per SM caps registers at 64: the rarely taken slow
 // paths of G-WFQ / G-WFQ-YMC may spill instead of halving occupancy.
-template <class T, int KIND>
+// REC: also record each successful operation's ticket (a.ticket); a separate
+// instantiation, so the timed kernels carry none of it.
+template <class T, int KIND, bool REC>
 __global__ void __launch_bounds__(256, 4) k_run(const __grid_constant__ gq_dev q, const __grid_constant__ RunK a) {
     const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
     u32 c_enq_ok = 0, c_full = 0, c_deq_ok = 0, c_empty = 0, c_err = 0;   // per-thread counts
@@ -62,18 +65,20 @@ __global__ void __launch_bounds__(256, 4) k_run(const __grid_constant__ gq_dev q
             const u64 tc = a.call ? globaltimer() : 0;
             int s;
             u64 v = 0;
+            u64 tk = ~0ull;
+            u64* const tkp = REC ? &tk : nullptr;
             if constexpr (KIND == GQ_YMC) {
                 // two operations with little in common: separate branches
                 if (is_enq) {
                     v = (sizeof(T) == 4) ? (((u64)t << 16) | seq) : (((u64)t << 32) | (u64)(seq + 1));
                     ++seq;
-                    s = queue_enqueue<T, KIND>(q, (T)v, t);
+                    s = queue_enqueue<T, KIND>(q, (T)v, t, tkp);
                     if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
                     else if (s == GQ_FULL) ++c_full;
                     else ++c_err;
                 } else {
                     T x = 0;
-                    s = queue_dequeue<T, KIND>(q, &x, t);
+                    s = queue_dequeue<T, KIND>(q, &x, t, tkp);
                     v = (s == GQ_OK) ? (u64)x : 0;
                     if (s == GQ_OK) { ++c_deq_ok; s_deq += v; }
                     else if (s == GQ_EMPTY) ++c_empty;
@@ -86,7 +91,7 @@ __global__ void __launch_bounds__(256, 4) k_run(const __grid_constant__ gq_dev q
                     ++seq;
                 }
                 T x = (T)v;
-                s = queue_op<T, KIND>(q, is_enq, &x, t);
+                s = queue_op<T, KIND>(q, is_enq, &x, t, tkp);
                 if (is_enq) {
                     if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
                     else if (s == GQ_FULL) ++c_full;
@@ -103,6 +108,7 @@ __global__ void __launch_bounds__(256, 4) k_run(const __grid_constant__ gq_dev q
             if (a.call) a.call[j] = tc;
             if (a.status) a.status[j] = (int8_t)s;
             if (a.val) a.val[j] = v;
+            if (REC) a.ticket[j] = (s == GQ_OK) ? tk : ~0ull;
         }
     }
     warp_add_full(&a.counts[GQ_CNT_ENQ_OK], c_enq_ok);
@@ -145,7 +151,7 @@ __global__ void k_drain(const __grid_constant__ gq_dev q, u64* out, u64 max, uns
     *count = k;
 }
 
-template <class T, int KIND>
+template <class T, int KIND, bool REC>
 int launch_run(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
     const u32 grid = (a.threads + block - 1) / block;
     // G-LFQ on a grid of at least two waves at 768 threads per SM: reserve
@@ -166,24 +172,29 @@ int launch_run(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
             // per_sm blocks fit, one more does not
             const int foot = (sm_bytes / (int)per_sm + sm_bytes / (int)(per_sm + 1)) / 2;
             smem = (size_t)std::min(std::max(foot - reserved, 0), optin);
-            if (smem && cudaFuncSetAttribute(k_run<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                            cudaSuccess) {
+            if (smem && cudaFuncSetAttribute(k_run<T, KIND, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem) != cudaSuccess) {
                 cudaGetLastError();
                 smem = 0;
             }
         }
     }
-    k_run<T, KIND><<<grid, block, smem, st>>>(h->dev, a);
+    k_run<T, KIND, REC><<<grid, block, smem, st>>>(h->dev, a);
     return gq_check_launch();
+}
+
+template <class T, bool REC>
+int dispatch_run_rec(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
+    switch (h->dev.kind) {
+        case GQ_LFQ: return launch_run<T, GQ_LFQ, REC>(h, a, block, st);
+        case GQ_WFQ: return launch_run<T, GQ_WFQ, REC>(h, a, block, st);
+        default: return launch_run<T, GQ_YMC, REC>(h, a, block, st);
+    }
 }
 
 template <class T>
 int dispatch_run(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
-    switch (h->dev.kind) {
-        case GQ_LFQ: return launch_run<T, GQ_LFQ>(h, a, block, st);
-        case GQ_WFQ: return launch_run<T, GQ_WFQ>(h, a, block, st);
-        default: return launch_run<T, GQ_YMC>(h, a, block, st);
-    }
+    return a.ticket ? dispatch_run_rec<T, true>(h, a, block, st) : dispatch_run_rec<T, false>(h, a, block, st);
 }
 
 template <class T>
@@ -366,6 +377,7 @@ extern "C" int gq_run(gq_handle h, const gq_run_args* args, void* stream) {
     a.call = reinterpret_cast<u64*>(g.d_call);
     a.end = reinterpret_cast<u64*>(g.d_end);
     a.counts = g.d_counts;
+    a.ticket = reinterpret_cast<u64*>(g.d_ticket);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return h->dev.elem_bytes == 4 ? dispatch_run<unsigned int>(h, a, g.block, st)
                                   : dispatch_run<unsigned long long>(h, a, g.block, st);

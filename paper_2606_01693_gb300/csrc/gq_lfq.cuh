@@ -82,8 +82,9 @@ __device__ __forceinline__ void ring_catchup(const gq_ring_view& r, u64 head) {
 
 // Inner-ring enqueue of index `idx` (TryEnq of Algorithm 1, retried until it
 // succeeds).  Returns GQ_OK, or GQ_ERR_TIMEOUT if the retry bound expires.
+// tk (nullable, test recorder): receives the ticket the index was installed at.
 template <bool MATCH>
-__device__ int lfq_ring_enq(const gq_dev& q, const gq_ring_view& r, u32 idx) {
+__device__ int lfq_ring_enq(const gq_dev& q, const gq_ring_view& r, u32 idx, u64* tk = nullptr) {
     for (u32 it = 0; it < kRetryLimit; ++it) {
         const u64 t = warp_faa<MATCH>(r.tail, 1, q.batch_width);
         u64* slot = r.slots + (t & q.slot_mask);
@@ -102,6 +103,7 @@ __device__ int lfq_ring_enq(const gq_dev& q, const gq_ring_view& r, u32 idx) {
         }
         if (done) {
             if (ld_rlx(r.threshold) != q.thr_reset) thr_reset(r.threshold, q.thr_reset, q.err);
+            if (tk) *tk = t;
             return GQ_OK;
         }
         if (q.backoff_ns) __nanosleep(q.backoff_ns);
@@ -111,9 +113,10 @@ __device__ int lfq_ring_enq(const gq_dev& q, const gq_ring_view& r, u32 idx) {
 }
 
 // Inner-ring dequeue (TryDeq of Algorithm 1, retried while it returns RETRY).
-// Returns GQ_OK with *idx, GQ_EMPTY, or GQ_ERR_TIMEOUT.
+// Returns GQ_OK with *idx, GQ_EMPTY, or GQ_ERR_TIMEOUT.  tk (nullable): the
+// ticket the index was taken at.
 template <bool MATCH>
-__device__ int lfq_ring_deq(const gq_dev& q, const gq_ring_view& r, u32* idx) {
+__device__ int lfq_ring_deq(const gq_dev& q, const gq_ring_view& r, u32* idx, u64* tk = nullptr) {
     if (ld_rlx(r.threshold) < 0) return GQ_EMPTY;
     for (u32 it = 0; it < kRetryLimit; ++it) {
         const u64 h = warp_faa<MATCH>(r.head, 1, q.batch_width);
@@ -125,6 +128,7 @@ __device__ int lfq_ring_deq(const gq_dev& q, const gq_ring_view& r, u32* idx) {
             if (ec == c) {
                 if (lfq_index(e) < kBotC) {          // Consume and return the index
                     *idx = lfq_index(e);
+                    if (tk) *tk = h;
                     // relaxed: the acquire load of e already ordered the payload read
                     if (!aref<u64>(*slot).compare_exchange_strong(e, (e & ~0xFFFFFFFFull) | kBotC, kRlx, kRlx))
                         aref<u64>(*slot).fetch_or(kBotC, kRlx);
@@ -164,8 +168,10 @@ __device__ __forceinline__ T data_load(const gq_dev& q, u32 i) {
     return aref<T>(static_cast<T*>(q.data)[i]).load(kRlx);
 }
 
+// tk (nullable, test recorder): the aq ticket of the operation (an item's
+// enqueue and its dequeue share it).
 template <class T, bool MATCH>
-__device__ int lfq_enqueue(const gq_dev& q, T v) {
+__device__ int lfq_enqueue(const gq_dev& q, T v, u64* tk = nullptr) {
     u32 i;
     int s = lfq_ring_deq<MATCH>(q, q.fq, &i);
     if (s == GQ_EMPTY) return GQ_FULL;
@@ -175,13 +181,13 @@ __device__ int lfq_enqueue(const gq_dev& q, T v) {
         return GQ_ERR_INVALID;
     }
     data_store<T>(q, i, v);                           // ordered before the release CAS in aq
-    return lfq_ring_enq<MATCH>(q, q.aq, i);
+    return lfq_ring_enq<MATCH>(q, q.aq, i, tk);
 }
 
 template <class T, bool MATCH>
-__device__ int lfq_dequeue(const gq_dev& q, T* v) {
+__device__ int lfq_dequeue(const gq_dev& q, T* v, u64* tk = nullptr) {
     u32 i;
-    int s = lfq_ring_deq<MATCH>(q, q.aq, &i);
+    int s = lfq_ring_deq<MATCH>(q, q.aq, &i, tk);
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {                            // never expected: a corrupt ring entry
         latch_error(q.err, GQ_ERR_INVALID);
@@ -200,11 +206,11 @@ __device__ int lfq_dequeue(const gq_dev& q, T* v) {
 // (divergent branches); WaveFAA groups the lanes by counter address.  Each
 // lane performs exactly the steps of its own operation.
 template <class T>
-__device__ int lfq_op(const gq_dev& q, bool enq, T* v) {
+__device__ int lfq_op(const gq_dev& q, bool enq, T* v, u64* tk = nullptr) {
     const gq_ring_view& from = enq ? q.fq : q.aq;
     const gq_ring_view& to = enq ? q.aq : q.fq;
     u32 i;
-    int s = lfq_ring_deq<true>(q, from, &i);
+    int s = lfq_ring_deq<true>(q, from, &i, enq ? nullptr : tk);
     if (s == GQ_EMPTY) return enq ? GQ_FULL : GQ_EMPTY;
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {                            // never expected: a corrupt ring entry
@@ -213,7 +219,7 @@ __device__ int lfq_op(const gq_dev& q, bool enq, T* v) {
     }
     if (enq) data_store<T>(q, i, *v);                 // ordered before the release CAS in aq
     else *v = data_load<T>(q, i);                     // after the acquire on the aq slot
-    return lfq_ring_enq<true>(q, to, i);
+    return lfq_ring_enq<true>(q, to, i, enq ? tk : nullptr);
 }
 
 }  // namespace gqd

@@ -453,13 +453,18 @@ static __device__ __noinline__ u64 wfq_slow_request(const gq_ring_view& R, const
 }
 
 
-// Inner-ring enqueue of index idx by thread `me`.
+// Inner-ring enqueue of index idx by thread `me`.  tk (nullable, test
+// recorder): the ticket the index was installed at, fast or slow.
 template <bool MATCH>
-__device__ int wfq_ring_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u32 me, u32 patience) {
+__device__ int wfq_ring_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u32 me, u32 patience,
+                            u64* tk = nullptr) {
     wfq_maybe_help(R, q, me);
     u64 t = 0;
     for (u32 p = 0; p < patience; ++p) {
-        if (wfq_try_enq<MATCH>(R, q, idx, &t) == kTryOk) return GQ_OK;
+        if (wfq_try_enq<MATCH>(R, q, idx, &t) == kTryOk) {
+            if (tk) *tk = t;
+            return GQ_OK;
+        }
         if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
     if (patience == 0) t = (g_cnt(ld_rlx(R.tail)) - 1) & kCntMask;   // a ticket value r never held
@@ -477,18 +482,24 @@ __device__ int wfq_ring_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u32
         if (w_cyc(e) != c || w_idx(e) != idx || (e & kWEnq)) break;
         if (cas(slot, e, e | kWEnq)) break;
     }
+    if (tk) *tk = tf;
     return GQ_OK;
 }
 
-// Inner-ring dequeue by thread `me`: GQ_OK with *idx, or GQ_EMPTY.
+// Inner-ring dequeue by thread `me`: GQ_OK with *idx, or GQ_EMPTY.  tk
+// (nullable): the ticket the index was taken at.
 template <bool MATCH>
-__device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u32 me, u32 patience) {
+__device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u32 me, u32 patience,
+                            u64* tk = nullptr) {
     if (ld_rlx(R.threshold) < 0) return GQ_EMPTY;
     wfq_maybe_help(R, q, me);
     u64 h = 0;
     for (u32 p = 0; p < patience; ++p) {
         const int s = wfq_try_deq<MATCH>(R, q, idx, &h);
-        if (s == kTryOk) return GQ_OK;
+        if (s == kTryOk) {
+            if (tk) *tk = h;
+            return GQ_OK;
+        }
         if (s == kTryEmpty) return GQ_EMPTY;
         if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
@@ -505,13 +516,15 @@ __device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u3
     const u64 e = ld_acq(slot);
     if (w_cyc(e) == c && w_idx(e) < kWBotC) {
         *idx = wfq_consume(R, slot, e, hf, q);
+        if (tk) *tk = hf;
         return GQ_OK;
     }
     return GQ_EMPTY;
 }
 
+// tk (nullable, test recorder): the aq ticket of the operation.
 template <class T, bool MATCH>
-__device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid) {
+__device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
@@ -525,17 +538,17 @@ __device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid) {
         return GQ_ERR_INVALID;
     }
     data_store<T>(q, i, v);
-    return wfq_ring_enq<MATCH>(q.aq, q, i, tid, q.patience_enq);
+    return wfq_ring_enq<MATCH>(q.aq, q, i, tid, q.patience_enq, tk);
 }
 
 template <class T, bool MATCH>
-__device__ int wfq_dequeue(const gq_dev& q, T* v, u32 tid) {
+__device__ int wfq_dequeue(const gq_dev& q, T* v, u32 tid, u64* tk = nullptr) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
     }
     u32 i;
-    int s = wfq_ring_deq<MATCH>(q.aq, q, &i, tid, q.patience_deq);
+    int s = wfq_ring_deq<MATCH>(q.aq, q, &i, tid, q.patience_deq, tk);
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {
         latch_error(q.err, GQ_ERR_INVALID);
@@ -549,7 +562,7 @@ __device__ int wfq_dequeue(const gq_dev& q, T* v, u32 tid) {
 // Enqueue or dequeue on one code path (see lfq_op): the rings are chosen per
 // lane, so mixed warps run both kinds of operation together.
 template <class T>
-__device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid) {
+__device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid, u64* tk = nullptr) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
@@ -557,7 +570,7 @@ __device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid) {
     const gq_ring_view& from = enq ? q.fq : q.aq;
     const gq_ring_view& to = enq ? q.aq : q.fq;
     u32 i;
-    int s = wfq_ring_deq<true>(from, q, &i, tid, q.patience_deq);
+    int s = wfq_ring_deq<true>(from, q, &i, tid, q.patience_deq, enq ? nullptr : tk);
     if (s == GQ_EMPTY) return enq ? GQ_FULL : GQ_EMPTY;
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {
@@ -566,7 +579,7 @@ __device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid) {
     }
     if (enq) data_store<T>(q, i, *v);
     else *v = data_load<T>(q, i);
-    return wfq_ring_enq<true>(to, q, i, tid, q.patience_enq);
+    return wfq_ring_enq<true>(to, q, i, tid, q.patience_enq, enq ? tk : nullptr);
 }
 
 }  // namespace gqd

@@ -165,7 +165,8 @@ static __device__ __noinline__ int ymc_help_enq(const gq_dev& q, u32 me, u64 i, 
 }
 
 // Slow enqueue of v by thread me whose fast path last failed at cell id.
-static __device__ __noinline__ int ymc_enq_slow(const gq_dev& q, u32 me, u64 v, u64 id) {
+// tk (nullable, test recorder): the cell the value was committed in.
+static __device__ __noinline__ int ymc_enq_slow(const gq_dev& q, u32 me, u64 v, u64 id, u64* tk) {
     u64* er = yrec(q, me);
     // release: a helper that reads this value must also see the commit of this
     // thread's previous request (its cell value), see ymc_help_enq
@@ -195,6 +196,7 @@ static __device__ __noinline__ int ymc_enq_slow(const gq_dev& q, u32 me, u64 v, 
     const u64 c = (u64)(-done);
     ymc_advance(q.ymc_tail, c);
     st_rel(q.cell_val + c, v);
+    if (tk) *tk = c;
     return GQ_OK;
 }
 
@@ -237,8 +239,10 @@ static __device__ __noinline__ void ymc_help_deq(const gq_dev& q, u32 me, u32 p)
 }
 
 
+// tk (nullable, test recorder): the cell of the operation (an item's enqueue
+// and its dequeue share it).
 template <class T, bool MATCH>
-__device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid) {
+__device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
@@ -250,15 +254,18 @@ __device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid) {
         const u64 i = warp_faa<MATCH>(q.ymc_tail, 1, q.batch_width);
         if (!ycell_ok(q, i)) return GQ_ERR_POOL_EXHAUSTED;
         u64 b = kVBot;
-        if (aref<u64>(q.cell_val[i]).compare_exchange_strong(b, x, kRel, kRlx)) return GQ_OK;
+        if (aref<u64>(q.cell_val[i]).compare_exchange_strong(b, x, kRel, kRlx)) {
+            if (tk) *tk = i;
+            return GQ_OK;
+        }
         id = i;
         if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
-    return ymc_enq_slow(q, tid, x, id);
+    return ymc_enq_slow(q, tid, x, id, tk);
 }
 
 template <class T, bool MATCH>
-__device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid) {
+__device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid, u64* tk = nullptr) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
@@ -291,6 +298,7 @@ __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid) {
         ymc_advance(q.ymc_head, c);
         v = ld_acq(q.cell_val + c);
         res = (v == kVTop) ? kYEmpty : kYValue;
+        id = c;
     }
     if (res == kYEmpty) return GQ_EMPTY;
     // every kYHelpDelay-th successful dequeue, help one peer's dequeue request
@@ -308,6 +316,7 @@ __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid) {
         mine[kYDh] = (u64)((peer + 1) % q.max_threads) | ((u64)(kYHelpDelay - 1) << 32);
         if (peer != tid) ymc_help_deq(q, tid, peer);
     }
+    if (tk) *tk = id;
     *out = (T)v;
     return GQ_OK;
 }

@@ -18,19 +18,21 @@ def make_queue(kind, cap, elem=8, max_threads=1 << 20, **opt):
 
 
 def run_log(q, mode, T, K=0, sched=None, producers=0, total_ops=0, block=256, record=True,
-            timestamps=False, delay_ns=0):
-    """Runs one driver launch; returns (kind, status, val, counts[, call, end]) as numpy, op-major."""
+            timestamps=False, delay_ns=0, tickets=False):
+    """Runs one driver launch; returns (kind, status, val, counts[, call, end][, ticket]) as numpy, op-major."""
     kmax = K if mode != gq.GQ_RUN_SPLIT else -(-total_ops // T)
     status = torch.full((kmax, T), -128, dtype=torch.int8, device=DEV) if record else None
     val = torch.zeros((kmax, T), dtype=torch.int64, device=DEV) if record else None
     call = torch.zeros((kmax, T), dtype=torch.int64, device=DEV) if timestamps else None
     end = torch.zeros((kmax, T), dtype=torch.int64, device=DEV) if timestamps else None
+    ticket = torch.zeros((kmax, T), dtype=torch.int64, device=DEV) if tickets else None
     counts = torch.zeros(8, dtype=torch.int64, device=DEV)
     dsched = None
     if sched is not None:
         dsched = torch.from_numpy(sched.view(np.int64)).to(DEV)
     gq.gq_run(q.handle, mode, T, block=block, ops=K, producers=producers, total_ops=total_ops,
-              sched=dsched, status=status, val=val, call=call, end=end, counts=counts, delay_ns=delay_ns)
+              sched=dsched, status=status, val=val, call=call, end=end, counts=counts, delay_ns=delay_ns,
+              ticket=ticket)
     st = q.sync_status()
     assert st == 0, gq.status_str(st)
     out = {"counts": u64(counts)}
@@ -41,6 +43,8 @@ def run_log(q, mode, T, K=0, sched=None, producers=0, total_ops=0, block=256, re
     if timestamps:
         out["call"] = u64(call)
         out["end"] = u64(end)
+    if tickets:
+        out["ticket"] = u64(ticket)
     return out
 
 
