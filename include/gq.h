@@ -180,13 +180,28 @@ int gq_sync_status(gq_handle h, void* stream);
 /* Copies the POD device view (for user kernels using gq_device.cuh). */
 int gq_device_view(gq_handle h, gq_dev* out);
 
-/* Rare-path event counters of a queue since its last reset (G-WFQ slow path):
- * requests published on the slow path, peer requests helped, and failed CAS
- * attempts on a Global word in SlowFAA.  Synchronous device-to-host copy. */
+/* Rare-path event counters of a queue since its last reset (G-WFQ slow path,
+ * Algorithm 2), and its ticket counters.  Synchronous device-to-host copies;
+ * read them while no kernel uses the queue.
+ *   slow_requests        requests published on the slow path
+ *   helps                peer requests helped
+ *   global_cas_failures  lost CASes on a Global word in SlowFAA
+ *   slow_rounds_tail/_head  successful SlowFAA rounds on the Tail / Head
+ *                        Global words of both rings (each advances that
+ *                        word's Counter by exactly one)
+ *   max_help_iterations  the most SlowFAA iterations one helper spent on one
+ *                        request
+ *   aq_head .. fq_tail   current ticket counters: G-LFQ the raw words, G-WFQ
+ *                        the Counter field of each Global word, G-WFQ-YMC H
+ *                        and T in aq_head / aq_tail (fq_* zero) */
 typedef struct {
     unsigned long long slow_requests;
     unsigned long long helps;
     unsigned long long global_cas_failures;
+    unsigned long long slow_rounds_tail;
+    unsigned long long slow_rounds_head;
+    unsigned long long max_help_iterations;
+    unsigned long long aq_head, aq_tail, fq_head, fq_tail;
 } gq_stats;
 int gq_get_stats(gq_handle h, gq_stats* out);
 

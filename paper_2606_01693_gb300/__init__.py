@@ -186,7 +186,10 @@ def gq_sync_status(h: int, stream=None) -> int:
 
 class gq_stats(ctypes.Structure):
     _fields_ = [("slow_requests", ctypes.c_uint64), ("helps", ctypes.c_uint64),
-                ("global_cas_failures", ctypes.c_uint64)]
+                ("global_cas_failures", ctypes.c_uint64), ("slow_rounds_tail", ctypes.c_uint64),
+                ("slow_rounds_head", ctypes.c_uint64), ("max_help_iterations", ctypes.c_uint64),
+                ("aq_head", ctypes.c_uint64), ("aq_tail", ctypes.c_uint64), ("fq_head", ctypes.c_uint64),
+                ("fq_tail", ctypes.c_uint64)]
 
 
 def gq_get_stats(h: int) -> dict:

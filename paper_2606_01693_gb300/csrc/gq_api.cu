@@ -421,11 +421,28 @@ extern "C" int gq_sync_status(gq_handle h, void* stream) {
 
 extern "C" int gq_get_stats(gq_handle h, gq_stats* out) {
     if (!h || !out) return GQ_ERR_INVALID;
-    unsigned long long w[4] = {0, 0, 0, 0};
+    unsigned long long w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (cudaMemcpy(w, h->dev.scratch, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return GQ_ERR_CUDA;
-    out->slow_requests = w[1];
-    out->helps = w[2];
-    out->global_cas_failures = w[3];
+    *out = gq_stats{};
+    out->slow_requests = w[kStatSlowRequests];
+    out->helps = w[kStatHelps];
+    out->global_cas_failures = w[kStatGlobalCasFail];
+    out->slow_rounds_tail = w[kStatSlowRoundsTail];
+    out->slow_rounds_head = w[kStatSlowRoundsHead];
+    out->max_help_iterations = w[kStatMaxHelpIters];
+    const gq_dev& d = h->dev;
+    unsigned long long* src[4] = {d.aq.head, d.aq.tail, d.fq.head, d.fq.tail};
+    if (d.kind == GQ_YMC) {
+        src[0] = d.ymc_head;
+        src[1] = d.ymc_tail;
+        src[2] = src[3] = nullptr;
+    }
+    unsigned long long* dst[4] = {&out->aq_head, &out->aq_tail, &out->fq_head, &out->fq_tail};
+    for (int i = 0; i < 4; ++i) {
+        if (!src[i]) continue;
+        if (cudaMemcpy(dst[i], src[i], 8, cudaMemcpyDeviceToHost) != cudaSuccess) return GQ_ERR_CUDA;
+        if (d.kind == GQ_WFQ) *dst[i] >>= kGThrBits;          // the Counter field of a Global word
+    }
     return GQ_OK;
 }
 

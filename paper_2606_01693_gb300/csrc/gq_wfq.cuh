@@ -103,8 +103,14 @@ enum : int {
 constexpr u32 kSlowStall = 1u << 16;
 constexpr u32 kSlowHard = 1u << 24;
 
-// Rare-path event counters kept in the queue's scratch line.
-enum { kStatSlowRequests = 1, kStatHelps = 2, kStatGlobalCasFail = 3 };
+// Rare-path event counters kept in the queue's scratch line: requests
+// published, peer requests helped, lost CASes on a Global word, successful
+// SlowFAA rounds per side (each advances Counter by exactly one), and the most
+// SlowFAA iterations one helper spent on one request.
+enum {
+    kStatSlowRequests = 1, kStatHelps = 2, kStatGlobalCasFail = 3,
+    kStatSlowRoundsTail = 4, kStatSlowRoundsHead = 5, kStatMaxHelpIters = 6
+};
 
 
 
@@ -180,6 +186,7 @@ static __device__ __noinline__ bool slow_faa(const gq_ring_view& R, int side, u3
         st_rel(P2, ((u64)(r + 1) << 43) | c);
         u64 gg = g;
         if (cas(G, gg, wfq_global(c + 1, me + 1))) {
+            if (q.scratch) atomicAdd(q.scratch + (side ? kStatSlowRoundsHead : kStatSlowRoundsTail), 1ull);
             if (thld) thr_dec(thld);
             u64 want = (c << 2) | kLInc;
             cas(L, want, c << 2);
@@ -391,11 +398,12 @@ static __device__ __noinline__ void wfq_help_request(const gq_ring_view& R, cons
     i64* thld = enq ? nullptr : R.threshold;
     u32 budget = kSlowHard;
     while (budget) {
-        if (!slow_faa(R, side, r, seq, me, &v, thld, q, &budget)) return;
+        if (!slow_faa(R, side, r, seq, me, &v, thld, q, &budget)) break;
         if (enq) wfq_try_enq_slow(R, q, r, v, idx);
         else wfq_try_deq_slow(R, q, r, v);
     }
-    latch_error(q.err, GQ_ERR_TIMEOUT);
+    if (q.scratch) atomicMax(q.scratch + kStatMaxHelpIters, (unsigned long long)(kSlowHard - budget));
+    if (!budget) latch_error(q.err, GQ_ERR_TIMEOUT);
 }
 
 // Inspects the next peer record (round robin) and helps it if a request is

@@ -108,3 +108,50 @@ def test_bulk_throughput_shape_with_slow_path_counts():
     assert rep["violations"] == 0, str(rep)
     st = q.stats()
     assert st["slow_requests"] < 0.01 * T * K, st
+
+
+def _delta(a, b):
+    return (b - a) % (1 << 43)          # Counter fields of the Global words are 43 bits
+
+
+@pytest.mark.parametrize("help_delay,delay_ns", [(1, 0), (64, 0), (2, 20000)])
+def test_slow_rounds_account_for_every_head_ticket(help_delay, delay_ns):
+    # Algorithm 2: a successful SlowFAA round advances the Global Counter by
+    # exactly one.  With patience 0 no fast-path fetch-add runs, so the two Head
+    # words move only by slow rounds (catch-up raises Tail words only): the
+    # Head tickets issued equal the slow rounds counted on the head side, and
+    # the Tail tickets issued are at least the tail-side rounds.
+    T, K = 1 << 11, 30
+    sched = synth.mixed_schedule_bits(29, T, K)
+    q = make_queue("wfq", 1 << 9, 8, max_threads=T, patience_enq=0, patience_deq=0, help_delay=help_delay)
+    s0 = q.stats()
+    r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched, delay_ns=delay_ns)
+    s1 = q.stats()
+    assert r["counts"][gq.GQ_CNT_ERRORS] == 0
+    heads = _delta(s0["aq_head"], s1["aq_head"]) + _delta(s0["fq_head"], s1["fq_head"])
+    tails = _delta(s0["aq_tail"], s1["aq_tail"]) + _delta(s0["fq_tail"], s1["fq_tail"])
+    assert s1["slow_rounds_head"] > 0 and heads == s1["slow_rounds_head"], (s0, s1)
+    assert s1["slow_rounds_tail"] > 0 and tails >= s1["slow_rounds_tail"], (s0, s1)
+    # every operation went slow on both of its rings
+    ok = int(r["counts"][gq.GQ_CNT_ENQ_OK] + r["counts"][gq.GQ_CNT_DEQ_OK])
+    assert s1["slow_requests"] >= 2 * ok
+    # wait-freedom, empirically: no helper came near the hard iteration cap;
+    # with all 2^11 threads on the slow path one helper needed at most about
+    # 31 k iterations (k = threads) for one request
+    print("max SlowFAA iterations of one helper on one request:", s1["max_help_iterations"])
+    assert 0 < s1["max_help_iterations"] <= 256 * T + (1 << 16)
+
+
+def test_fast_path_tickets_outnumber_slow_rounds():
+    # default patience: fetch-adds issue most tickets, SlowFAA rounds are a subset
+    T, K = 1 << 16, 64
+    sched = synth.mixed_schedule_bits(31, T, K)
+    q = make_queue("wfq", 1 << 12, 8, max_threads=T)
+    s0 = q.stats()
+    r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched, record=False)
+    s1 = q.stats()
+    heads = _delta(s0["aq_head"], s1["aq_head"]) + _delta(s0["fq_head"], s1["fq_head"])
+    tails = _delta(s0["aq_tail"], s1["aq_tail"]) + _delta(s0["fq_tail"], s1["fq_tail"])
+    # a successful operation takes at least one Head ticket (fq for an enqueue, aq for a dequeue)
+    assert heads >= int(r["counts"][gq.GQ_CNT_ENQ_OK] + r["counts"][gq.GQ_CNT_DEQ_OK])
+    assert s1["slow_rounds_head"] <= heads and s1["slow_rounds_tail"] <= tails
