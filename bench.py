@@ -41,7 +41,7 @@ CAPACITY = 1 << 20
 # capture of `bench.py --steps 1 --warmup 3 --no-sweep --no-e2e --no-cpu --no-apps --no-batched
 # --no-serving` with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass; profiles/).
 # Set to None whenever the kernels change.
-NCU_TRAFFIC = {"lfq": 46732288 + 5220096, "wfq": 63570944 + 206347776, "ymc": 986342912 + 825717760}
+NCU_TRAFFIC = {"lfq": 46720768 + 5173504, "wfq": 63858432 + 167825152, "ymc": 986330368 + 824618240}
 
 
 def parse():
