@@ -79,9 +79,13 @@ typedef struct {
                               /* Non-null selects a separate recording kernel.           */
 } gq_run_args;
 
-/* Launches the driver kernel.  For SPLIT, ops per thread = ceil(total_ops /
- * threads) bounds the op-major arrays; threads t >= total_ops mod threads do
- * floor(total_ops / threads) ops.  G-WFQ / G-WFQ-YMC need threads <= max_threads.
+/* Launches the driver kernel (blocks of at most 256 threads).  For SPLIT, ops
+ * per thread = ceil(total_ops / threads) bounds the op-major arrays; threads
+ * t >= total_ops mod threads do floor(total_ops / threads) ops.  G-WFQ /
+ * G-WFQ-YMC need threads <= max_threads.  A G-LFQ grid of at least two waves
+ * of 768 threads per SM is launched with unused dynamic shared memory that
+ * holds residency to 768 threads per SM (fewer requests queue at the hot L2
+ * lines; the results do not depend on it).
  * Errors: GQ_ERR_INVALID, GQ_ERR_TOO_MANY_THREADS, GQ_ERR_CUDA. */
 int gq_run(gq_handle h, const gq_run_args* args, void* stream);
 
