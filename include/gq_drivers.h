@@ -58,7 +58,7 @@ enum {
 typedef struct {
     uint32_t mode;            /* GQ_RUN_*                                                  */
     uint32_t threads;         /* logical threads (one device thread each)                 */
-    uint32_t block;           /* threads per block (multiple of 32, <= 1024)               */
+    uint32_t block;           /* threads per block (multiple of 32, <= 256)                */
     uint32_t ops;             /* PAIRS/MIXED: operations per thread (PAIRS: even)          */
     uint32_t producers;       /* SPLIT: threads [0, producers) enqueue                     */
     uint32_t delay_ns;        /* > 0: each op waits a pseudo-random 0..delay_ns-1 ns first */
@@ -79,7 +79,7 @@ typedef struct {
                               /* Non-null selects a separate recording kernel.           */
 } gq_run_args;
 
-/* Launches the driver kernel (blocks of at most 256 threads).  For SPLIT, ops
+/* Launches the driver kernel.  For SPLIT, ops
  * per thread = ceil(total_ops / threads) bounds the op-major arrays; threads
  * t >= total_ops mod threads do floor(total_ops / threads) ops.  G-WFQ /
  * G-WFQ-YMC need threads <= max_threads.  A G-LFQ grid of at least two waves

@@ -354,7 +354,7 @@ extern "C" int gq_run(gq_handle h, const gq_run_args* args, void* stream) {
     if (!h || !args || !args->d_counts) return GQ_ERR_INVALID;
     const gq_run_args& g = *args;
     if (g.mode > GQ_RUN_SPLIT || g.threads == 0) return GQ_ERR_INVALID;
-    if (g.block == 0 || g.block > 1024 || (g.block & 31)) return GQ_ERR_INVALID;
+    if (g.block == 0 || g.block > 256 || (g.block & 31)) return GQ_ERR_INVALID;
     if (g.mode == GQ_RUN_MIXED && !g.d_sched) return GQ_ERR_INVALID;
     if (g.mode == GQ_RUN_PAIRS && (g.ops & 1)) return GQ_ERR_INVALID;
     if (g.mode == GQ_RUN_SPLIT && (g.producers > g.threads || g.total_ops / g.threads >= (1ull << 32)))
