@@ -148,7 +148,7 @@ typedef struct {
     uint32_t nqueues;
     uint32_t threads_per_queue;    /* logical threads of each queue, multiple of 32       */
     uint32_t producers_per_queue;  /* the first this many of each queue's threads enqueue */
-    uint32_t block;                /* threads per block, multiple of 32                    */
+    uint32_t block;                /* threads per block, multiple of 32, <= 256           */
     uint32_t blocks;               /* grid size; 0 = every resident block                  */
     uint32_t kind, elem_bytes;     /* must match the views                                 */
     uint32_t reserved;

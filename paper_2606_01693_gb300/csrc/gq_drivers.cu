@@ -328,7 +328,7 @@ extern "C" int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void*
 extern "C" int gq_run_multi(const void* d_views, const gq_multi_args* args, void* stream) {
     if (!d_views || !args || !args->d_counts || !args->nqueues) return GQ_ERR_INVALID;
     const gq_multi_args& g = *args;
-    if (g.threads_per_queue == 0 || (g.threads_per_queue & 31) || g.block == 0 || g.block > 1024 || (g.block & 31) ||
+    if (g.threads_per_queue == 0 || (g.threads_per_queue & 31) || g.block == 0 || g.block > 256 || (g.block & 31) ||
         g.producers_per_queue > g.threads_per_queue || g.kind > GQ_YMC || (g.elem_bytes != 4 && g.elem_bytes != 8))
         return GQ_ERR_INVALID;
     if (g.elem_bytes == 4 && ((uint64_t)g.nqueues * g.threads_per_queue > 65536 ||
