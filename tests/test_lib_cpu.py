@@ -134,3 +134,31 @@ def test_wavefaa_probe_arguments_validated():
         assert L.gq_wavefaa_probe(p, 64, width, p, p, None) == gq.GQ_ERR_INVALID
     assert L.gq_wavefaa_probe(p, 0, 32, p, p, None) == gq.GQ_ERR_INVALID
     assert L.gq_wavefaa_probe(None, 64, 32, p, p, None) == gq.GQ_ERR_INVALID
+
+
+def test_run_multi_arguments_validated():
+    L = gq.load()
+    views = ctypes.c_void_p(0x1000)   # never dereferenced: every call below fails validation first
+    good = dict(nqueues=4, threads_per_queue=64, producers_per_queue=32, block=256, blocks=0, kind=gq.KINDS["lfq"],
+                elem_bytes=8, reserved=0, ops_per_queue=1000, d_counts=0x2000)
+    bad = [dict(block=512), dict(block=0), dict(block=48), dict(threads_per_queue=48),
+           dict(producers_per_queue=65), dict(kind=3), dict(elem_bytes=2), dict(nqueues=0), dict(d_counts=None)]
+    for change in bad:
+        a = gq.gq_multi_args(**dict(good, **change))
+        assert L.gq_run_multi(views, ctypes.byref(a), None) == gq.GQ_ERR_INVALID, change
+
+
+def test_run_rejects_null_arguments():
+    L = gq.load()
+    a = gq.gq_run_args(gq.GQ_RUN_PAIRS, 256, 256, 2, 0, 0, 0, None, None, None, None, None, 0x1000, None)
+    assert L.gq_run(None, ctypes.byref(a), None) == gq.GQ_ERR_INVALID
+    a.d_counts = None
+    assert L.gq_run(ctypes.c_void_p(0x1000), ctypes.byref(a), None) == gq.GQ_ERR_INVALID
+
+
+def test_run_rejects_bad_launch_shape():
+    L = gq.load()
+    h = ctypes.c_void_p(0x1000)   # never dereferenced: the launch shape is checked first
+    for block, threads, ops in [(512, 256, 2), (48, 256, 2), (0, 256, 2), (256, 0, 2), (256, 256, 3)]:
+        a = gq.gq_run_args(gq.GQ_RUN_PAIRS, threads, block, ops, 0, 0, 0, None, None, None, None, None, 0x2000, None)
+        assert L.gq_run(h, ctypes.byref(a), None) == gq.GQ_ERR_INVALID, (block, threads, ops)
