@@ -296,7 +296,11 @@ extern "C" int gq_create(int kind, uint64_t capacity, uint32_t elem_bytes, uint3
     h->opt = o;
     h->lay = make_layout(kind, capacity, elem_bytes, max_threads);
     if (cudaGetDevice(&h->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess ||
+        gq_run_kernels_init(h->device, h->smem_optin) != GQ_OK) {
         delete h;
         return GQ_ERR_CUDA;
     }

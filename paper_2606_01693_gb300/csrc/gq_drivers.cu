@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "../../include/gq_drivers.h"
 #include "gq_host.h"
@@ -163,24 +164,21 @@ int launch_run(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
     size_t smem = 0;
     if (KIND == GQ_LFQ) {
         const u32 per_sm = block >= 768 ? 1u : 768u / block;
-        int sm_bytes = 0, reserved = 0, optin = 0;
-        if ((u64)grid >= 2ull * per_sm * (u64)h->sm_count &&
-            cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device) == cudaSuccess &&
-            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, h->device) == cudaSuccess &&
-            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) == cudaSuccess) {
+        if ((u64)grid >= 2ull * per_sm * (u64)h->sm_count && h->smem_per_sm > 0) {
             // a block's footprint halfway between sm/(per_sm + 1) and sm/per_sm:
             // per_sm blocks fit, one more does not
+            const int sm_bytes = h->smem_per_sm;
             const int foot = (sm_bytes / (int)per_sm + sm_bytes / (int)(per_sm + 1)) / 2;
-            smem = (size_t)std::min(std::max(foot - reserved, 0), optin);
-            if (smem && cudaFuncSetAttribute(k_run<T, KIND, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem) != cudaSuccess) {
-                cudaGetLastError();
-                smem = 0;
-            }
+            smem = (size_t)std::min(std::max(foot - h->smem_reserved, 0), h->smem_optin);
         }
     }
     k_run<T, KIND, REC><<<grid, block, smem, st>>>(h->dev, a);
     return gq_check_launch();
+}
+
+template <class T, bool REC>
+cudaError_t allow_run_smem(int bytes) {
+    return cudaFuncSetAttribute(k_run<T, GQ_LFQ, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <class T, bool REC>
@@ -348,6 +346,20 @@ extern "C" int gq_run_multi(const void* d_views, const gq_multi_args* args, void
         case GQ_WFQ: return launch_multi<unsigned long long, GQ_WFQ>(v, g, st);
         default: return launch_multi<unsigned long long, GQ_YMC>(v, g, st);
     }
+}
+
+int gq_run_kernels_init(int device, int smem_optin) {
+    static std::atomic<int> done[64];
+    if (device >= 0 && device < 64 && done[device].load(std::memory_order_acquire)) return GQ_OK;
+    if (allow_run_smem<unsigned int, false>(smem_optin) != cudaSuccess ||
+        allow_run_smem<unsigned int, true>(smem_optin) != cudaSuccess ||
+        allow_run_smem<unsigned long long, false>(smem_optin) != cudaSuccess ||
+        allow_run_smem<unsigned long long, true>(smem_optin) != cudaSuccess) {
+        cudaGetLastError();
+        return GQ_ERR_CUDA;
+    }
+    if (device >= 0 && device < 64) done[device].store(1, std::memory_order_release);
+    return GQ_OK;
 }
 
 extern "C" int gq_run(gq_handle h, const gq_run_args* args, void* stream) {

@@ -44,6 +44,7 @@ struct gq_queue {
     bool owned;
     int device;
     int sm_count;
+    int smem_per_sm, smem_reserved, smem_optin;   // shared memory per SM, reserved per block, per-block maximum
     uint64_t start_ticket;
     void* aux;            // library-owned device scratch of the applications (gq_bfs), made on first use
     uint64_t aux_bytes;
@@ -51,6 +52,12 @@ struct gq_queue {
 
 // Status helpers
 int gq_check_launch();
+
+// Once per device (gq_create calls it, outside any stream capture): lets the
+// G-LFQ run kernels take dynamic shared memory up to the per-block maximum, so
+// that their residency-capped launches need no attribute call later (a launch
+// being captured into a CUDA graph then makes none).
+int gq_run_kernels_init(int device, int smem_optin);
 
 // Launch configuration for a grid-stride kernel whose threads need one record
 // each (G-WFQ, G-WFQ-YMC): never more threads than records.

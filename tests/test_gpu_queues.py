@@ -255,3 +255,25 @@ def test_caller_owned_workspace(kind):
     q.reset()
     q.dequeue(out, None, ok)
     assert q.sync_status() == 0 and int(ok.item()) == 0
+
+
+def test_capped_run_captured_in_a_graph():
+    # a G-LFQ run of 2^18 threads (1024 blocks) is launched with the residency
+    # cap; made only inside stream capture, it replays like an eager launch
+    # (pairs: zero FULL, zero EMPTY, sums agree)
+    T = 1 << 18
+    q = make_queue("lfq", T, 8, max_threads=T)
+    counts = torch.zeros(8, dtype=torch.int64, device=DEV)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        q.reset()
+        counts.zero_()
+        gq.gq_run(q.handle, gq.GQ_RUN_PAIRS, T, block=256, ops=4, counts=counts)
+    for _ in range(3):
+        g.replay()
+        torch.cuda.synchronize()
+        c = u64(counts)
+        assert c[gq.GQ_CNT_ENQ_OK] == 2 * T and c[gq.GQ_CNT_DEQ_OK] == 2 * T, c
+        assert c[gq.GQ_CNT_ENQ_FULL] == 0 and c[gq.GQ_CNT_DEQ_EMPTY] == 0 and c[gq.GQ_CNT_ERRORS] == 0
+        assert c[gq.GQ_CNT_SUM_ENQ] == c[gq.GQ_CNT_SUM_DEQ]
+    assert q.sync_status() == 0
