@@ -270,6 +270,9 @@ __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid, u64* tk = nullptr) 
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
     }
+    // the help countdown is private to this thread: load it first so that its
+    // latency overlaps the operation instead of following it
+    const u64 w = yrec(q, tid)[kYDh];         // next peer | countdown << 32
     u64 id = 0, v = 0;
     int res = kYUnusable;
     for (u32 p = 0; p <= q.patience_deq && res == kYUnusable; ++p) {
@@ -307,7 +310,6 @@ __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid, u64* tk = nullptr) 
     // pending request is inspected within k * D dequeues of any thread) and
     // saves the record load on the other D - 1 (+10 % at 2^20 threads).
     u64* mine = yrec(q, tid);
-    const u64 w = mine[kYDh];                 // private: next peer | countdown << 32
     const u32 left = (u32)(w >> 32);
     if (left) {
         mine[kYDh] = w - (1ull << 32);
