@@ -41,7 +41,7 @@ CAPACITY = 1 << 20
 # capture of `bench.py --steps 1 --warmup 3 --no-sweep --no-e2e --no-cpu --no-apps --no-batched
 # --no-serving` with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass; profiles/).
 # Set to None whenever the kernels change.
-NCU_TRAFFIC = {"lfq": 46720768 + 5173504, "wfq": 63858432 + 167825152, "ymc": 986330368 + 824618240}
+NCU_TRAFFIC = {"lfq": 46698240 + 5093632, "wfq": 63643648 + 167041024, "ymc": 987250688 + 825881088}
 
 
 def parse():
