@@ -53,6 +53,13 @@ constexpr u64 kRefBot = 0, kRefTop = 1;
 constexpr u32 kYHelpDelay = 64;   // successful dequeues per peer inspection
 constexpr u32 kYSpin = 16;      // back-to-back reads of an empty cell (its enqueuer may be on its way)
 constexpr u32 kYWaitPolls = 256; // then, if T shows the ticket taken, polls 64 ns apart
+// Cells one helper may visit in a dequeue request's candidate search.  Every
+// step moves to the next cell, so the search always progresses; it can be long
+// when the request's cell lies far below T (cells below T hold claimed values
+// or were marked unusable while T passed them: 2^12 threads, 90 % consumers,
+// patience 0 scanned more than 2^16 cells).  The bound only stops a search that
+// has run through millions of cells.
+constexpr u32 kYScanLimit = 1u << 22;
 
 enum : int {
     kYErId = 0,    // enqueue request: > 0 pending from cell id on, < 0 done at cell -id
@@ -210,7 +217,7 @@ static __device__ __noinline__ void ymc_help_deq(const gq_dev& q, u32 me, u32 p)
     for (u32 it = 0; it < kRetryLimit; ++it) {
         // find a candidate cell, unless one gets announced meanwhile
         u32 jt = 0;
-        for (; jt < kRetryLimit && idx == old && cand == 0; ++jt) {
+        for (; jt < kYScanLimit && idx == old && cand == 0; ++jt) {
             ++i;
             if (!ycell_ok(q, (u64)i)) return;
             u64 v;
@@ -218,7 +225,7 @@ static __device__ __noinline__ void ymc_help_deq(const gq_dev& q, u32 me, u32 p)
             if (s == kYEmpty || (s == kYValue && ld_acq(q.cell_deq + i) == kRefBot)) cand = i;
             else idx = ld_i(dr + kYDrIdx);
         }
-        if (jt == kRetryLimit) break;   // never claim the request's own first cell unannounced
+        if (jt == kYScanLimit) break;   // never claim the request's own first cell unannounced
         if (cand != 0) {
             u64 cur = (u64)idx;
             if (cas(dr + kYDrIdx, cur, (u64)cand)) idx = cand;

@@ -85,3 +85,18 @@ def test_reserved_payloads_rejected():
     q.dequeue(out, None, ok)
     assert q.sync_status() == 0
     assert sorted(out[: int(ok.item())].cpu().tolist()) == [5, 7]
+
+
+@pytest.mark.parametrize("T", [1 << 12, 1 << 14])
+def test_slow_dequeues_on_an_empty_heavy_split(T):
+    # 90 % consumers with patience 0: the queue is empty most of the time, T
+    # runs past the cells of published dequeue requests, and their candidate
+    # searches walk more than 2^16 cells before they reach an empty cell
+    q = make_queue("ymc", 1 << 26, 8, max_threads=T, patience_enq=0, patience_deq=0)
+    P = T // 10
+    r = run_log(q, gq.GQ_RUN_SPLIT, T, producers=P, total_ops=24 * T)
+    left = drain(q, 24 * T)
+    rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
+    assert rep["violations"] == 0, str(rep)
+    assert r["counts"][gq.GQ_CNT_ERRORS] == 0
+    assert rep["deq_empty"] > 0
