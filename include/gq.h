@@ -219,6 +219,10 @@ int gq_info(gq_handle h, uint64_t* workspace_bytes, int* library_owned);
  * *d_num_out is overwritten with their number (n when nothing fails).  Same
  * result as gq_create + gq_enqueue_batch + gq_dequeue_batch on a G-LFQ of
  * capacity >= n, without gq_create's allocation.
+ *   A device-side failure inside the call (a bounded wait that expired) is
+ *   reported only through the count: the call returns before its kernels
+ *   run and the next call clears the array's error word, so *d_num_out < n
+ *   is the sign of it (with nothing failing every item comes back).
  *   n <= 65536 (the array's capacity); larger n returns GQ_ERR_INVALID before
  *   any work is launched.  d_items, d_out: n 8-byte elements; d_num_out: one
  *   8-byte counter; all caller-owned device memory.

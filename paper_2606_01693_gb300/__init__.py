@@ -133,6 +133,27 @@ def _ptr(t) -> int | None:
     return t.data_ptr()
 
 
+def _need(t, n: int, elem: int, what: str) -> None:
+    """Checks a buffer before its address crosses the C ABI: a contiguous CUDA
+    tensor with room for n elements of `elem` bytes.  Raw integer addresses
+    and None (nullable arguments) pass unchecked."""
+    if t is None or isinstance(t, int):
+        return
+    if not getattr(t, "is_cuda", False):
+        raise GqError(GQ_ERR_INVALID, what + " (not a CUDA tensor)")
+    if not t.is_contiguous():
+        raise GqError(GQ_ERR_INVALID, what + " (not contiguous)")
+    if t.numel() * t.element_size() < n * elem:
+        raise GqError(GQ_ERR_INVALID, what + " (holds %d bytes, needs %d)" % (t.numel() * t.element_size(), n * elem))
+
+
+def _elem_bytes(h: int) -> int:
+    """Payload width of a queue handle, read from its device view."""
+    buf = (ctypes.c_uint8 * GQ_VIEW_BYTES)()
+    _check(load().gq_device_view(h, buf), "gq_device_view")
+    return int.from_bytes(bytes(buf[4:8]), "little")
+
+
 def _stream(stream=None) -> int | None:
     if stream is not None:
         return stream if isinstance(stream, int) else stream.cuda_stream
@@ -168,13 +189,21 @@ def gq_reset(h: int, stream=None) -> None:
 
 
 def gq_enqueue_batch(h: int, items, n: int | None = None, status=None, num_ok=None, stream=None) -> None:
-    n = items.numel() if n is None else n
+    eb = _elem_bytes(h)
+    n = items.numel() * items.element_size() // eb if n is None else n
+    _need(items, n, eb, "gq_enqueue_batch: items")
+    _need(status, n, 1, "gq_enqueue_batch: status")
+    _need(num_ok, 1, 8, "gq_enqueue_batch: num_ok")
     _check(load().gq_enqueue_batch(h, _ptr(items), n, _ptr(status), _ptr(num_ok), _stream(stream)),
            "gq_enqueue_batch")
 
 
 def gq_dequeue_batch(h: int, out, n: int | None = None, status=None, num_ok=None, stream=None) -> None:
-    n = out.numel() if n is None else n
+    eb = _elem_bytes(h)
+    n = out.numel() * out.element_size() // eb if n is None else n
+    _need(out, n, eb, "gq_dequeue_batch: out")
+    _need(status, n, 1, "gq_dequeue_batch: status")
+    _need(num_ok, 1, 8, "gq_dequeue_batch: num_ok")
     _check(load().gq_dequeue_batch(h, _ptr(out), n, _ptr(status), _ptr(num_ok), _stream(stream)),
            "gq_dequeue_batch")
 
@@ -236,6 +265,9 @@ def gq_wavefaa_probe(take, width: int, counters, tickets, stream=None) -> None:
 def gq_fifo_static_roundtrip(items, out, num_out, n: int | None = None, stream=None) -> None:
     """FIFO round trip on the library's static device array (no allocation; n <= 65536)."""
     n = items.numel() if n is None else n
+    _need(items, n, 8, "gq_fifo_static_roundtrip: items")
+    _need(out, n, 8, "gq_fifo_static_roundtrip: out")
+    _need(num_out, 1, 8, "gq_fifo_static_roundtrip: num_out")
     _check(load().gq_fifo_static_roundtrip(_ptr(items), n, _ptr(out), _ptr(num_out), _stream(stream)),
            "gq_fifo_static_roundtrip")
 

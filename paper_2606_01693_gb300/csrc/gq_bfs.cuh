@@ -322,7 +322,9 @@ __device__ bool level_chunks(const gq_dev& nxt, const LevelCtx& c, u32* cnt, u64
 // frontier queues qa / qb (left empty).  ctl[0..2]: rotating frontier counts;
 // table: this cluster's chunk map of `cap` positions.  Returns the number of
 // levels; adds scanned edges to *edges; a chunk wait that expired is latched
-// in *err (nullable).
+// in *err (nullable) as 1.  That is the only failure of the chunk phase: a
+// vertex whose chunks do not fit in the map is scanned by the gather instead
+// (chunk_publish), so a full map is not an error.
 template <int KIND>
 __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* table, u64 cap,
                            const gq_bfs_instance& g, u32* dist, u32 ct, u32 nct, cg::cluster_group& cluster,

@@ -21,9 +21,9 @@
 //            EMPTY when T <= h); a value is taken by CAS deq[h] 0 -> 1.
 // Slow paths publish the request in the record and are completed by helpers:
 //   enqueue: the owner keeps taking tickets and offering its request to cells
-//            (CAS enq[i] 0 -> r+2); a dequeuer that finds an unusable cell with
-//            a request attached claims that cell for the request (CAS id -> -i)
-//            and commits the value there.  Dequeuers also attach pending peer
+//            (CAS enq[i] 0 -> (id << 24) | (r + 1)); a dequeuer that finds an
+//            unusable cell with a request attached claims that cell for the
+//            request (CAS id -> -i) and commits the value there.  Dequeuers also attach pending peer
 //            requests to cells they find empty (round-robin over peers).
 //   dequeue: helpers scan cells after the request's id for a candidate (a
 //            value not yet taken, or an EMPTY decision), announce it in idx and

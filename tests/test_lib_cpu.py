@@ -162,3 +162,38 @@ def test_run_rejects_bad_launch_shape():
     for block, threads, ops in [(512, 256, 2), (48, 256, 2), (0, 256, 2), (256, 0, 2), (256, 256, 3)]:
         a = gq.gq_run_args(gq.GQ_RUN_PAIRS, threads, block, ops, 0, 0, 0, None, None, None, None, None, 0x2000, None)
         assert L.gq_run(h, ctypes.byref(a), None) == gq.GQ_ERR_INVALID, (block, threads, ops)
+
+
+def test_binding_checks_buffers_before_the_call():
+    # host tensors, undersized outputs and short counters never reach the C ABI
+    import torch
+    items = torch.zeros(16, dtype=torch.int64)
+    with pytest.raises(gq.GqError) as ei:
+        gq.gq_fifo_static_roundtrip(items, items, items[:1])
+    assert ei.value.status == gq.GQ_ERR_INVALID and "CUDA" in str(ei.value)
+
+    class FakeCuda:
+        """Stands in for a CUDA tensor of the given size (no GPU here)."""
+        is_cuda = True
+
+        def __init__(self, n, es=8):
+            self.n, self.es = n, es
+
+        def numel(self):
+            return self.n
+
+        def element_size(self):
+            return self.es
+
+        def is_contiguous(self):
+            return True
+
+        def data_ptr(self):
+            return 0
+
+    with pytest.raises(gq.GqError, match="out"):
+        gq.gq_fifo_static_roundtrip(FakeCuda(16), FakeCuda(8), FakeCuda(1))
+    with pytest.raises(gq.GqError, match="num_out"):
+        gq.gq_fifo_static_roundtrip(FakeCuda(16), FakeCuda(16), FakeCuda(1, 4))
+    with pytest.raises(gq.GqError, match="items"):
+        gq.gq_fifo_static_roundtrip(FakeCuda(16, 4), FakeCuda(16), FakeCuda(1), n=16)
