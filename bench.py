@@ -497,6 +497,13 @@ def main():
     value = all_succ / (total_ms * 1e-3) / 1e6
 
     # ---- roofline of the dominant run kernel ----
+    # Section III: a successful ring operation (G-LFQ, G-WFQ) is two slot RMWs
+    # (one per index ring) and 2/W counter fetch-and-adds; a G-WFQ-YMC one is one
+    # cell RMW (the value CAS, or the dequeue's claim) and 1/W fetch-and-add.
+    # Two ceilings bound the rate: the slots' (coalesced-CAS rate / slot RMWs per
+    # op) and the hot counters' (each counter serves W tickets per fetch-and-add
+    # at the single-address rate; a balanced run spreads its operations over two
+    # counters per direction, 2 W P_single).  The binding one is the smaller.
     W = 32
     per_queue = {}
     for k in kinds:
@@ -505,23 +512,83 @@ def main():
         slot_rmw = 1.0 if k == "ymc" else 2.0
         ctr_per_op = (1.0 if k == "ymc" else 2.0) / W
         atom_rate = ops_s * (slot_rmw + ctr_per_op)
-        peak_atom = peaks["coalesced_cas_gops"] * 1e9
+        slot_ceiling = peaks["coalesced_cas_gops"] * 1e9 / slot_rmw
         counter_ceiling = 2 * W * peaks["same_addr_faa_gops"] * 1e9
+        ceiling = min(slot_ceiling, counter_ceiling)
         per_queue[k] = {"kernel_mops": ops_s / 1e6, "kernel_ms_per_launch": kern_ms[k] / args.steps,
                         "succ_ops_per_launch": succ[k] // args.steps,
-                        "atomics_per_succ_op": slot_rmw + ctr_per_op,
+                        "algorithmic_atomics_per_succ_op": slot_rmw + ctr_per_op,
                         "achieved_gatomic_s": atom_rate / 1e9,
-                        "frac_of_coalesced_cas_peak": atom_rate / peak_atom,
-                        "counter_ceiling_mops": counter_ceiling / 1e6,
+                        "slot_ceiling_mops": slot_ceiling / 1e6, "counter_ceiling_mops": counter_ceiling / 1e6,
+                        "binding": "counter" if counter_ceiling < slot_ceiling else "slot",
+                        "frac_of_binding_ceiling": ops_s / ceiling,
                         "empty": int(c[k][gq.GQ_CNT_DEQ_EMPTY]) // args.steps,
                         "full": int(c[k][gq.GQ_CNT_ENQ_FULL]) // args.steps}
+    # measured fast-path events per successful operation: one launch of the
+    # counting instantiation on the same workload (never timed)
+    for k in kinds:
+        oc = torch.zeros(gq.GQ_OC_N, dtype=torch.int64, device=dev)
+        cc = torch.zeros(8, dtype=torch.int64, device=dev)
+        queues[k].reset()
+        gq.gq_run(queues[k].handle, gq.GQ_RUN_MIXED, T, block=256, ops=K, sched=dsched, counts=cc, opcount=oc)
+        torch.cuda.synchronize()
+        cn = cc.cpu().numpy()
+        s_ok = float(cn[gq.GQ_CNT_ENQ_OK] + cn[gq.GQ_CNT_DEQ_OK])
+        o = dict(zip(gq.OC_NAMES, oc.cpu().numpy().tolist()))
+        atomics = o["faa"] + o["cas"] + o["rmw"] + o["threshold"] + o["catchup"]
+        per_queue[k]["measured"] = {"atomics_per_succ_op": round(atomics / s_ok, 4),
+                                    "per_succ_op": {nm: round(v / s_ok, 4) for nm, v in o.items()},
+                                    "cas_fail_frac": round(o["cas_fail"] / max(1, o["cas"]), 4)}
     dom = max(kinds, key=lambda k: kern_ms[k])
     pq = per_queue[dom]
     traffic = NCU_TRAFFIC.get(dom)
+    bind = min(pq["slot_ceiling_mops"], pq["counter_ceiling_mops"])
     roofline = {"bound": "l2_atomic", "kernel": "k_run<u64,%s> (mixed 50/50)" % dom.upper(),
-                "achieved": pq["achieved_gatomic_s"], "peak": peaks["coalesced_cas_gops"],
-                "unit": "Gatomic/s", "frac": pq["frac_of_coalesced_cas_peak"], "traffic": traffic,
-                "peak_source": "measured live: warp-coalesced 64-bit CAS on an L2-resident 16 MiB buffer"}
+                "achieved": pq["kernel_mops"] / 1e3, "peak": bind / 1e3, "unit": "G succ ops/s",
+                "frac": pq["frac_of_binding_ceiling"], "traffic": traffic,
+                "binding": pq["binding"],
+                "slot_ceiling": pq["slot_ceiling_mops"] / 1e3, "counter_ceiling": pq["counter_ceiling_mops"] / 1e3,
+                "achieved_gatomic_s": pq["achieved_gatomic_s"],
+                "frac_of_coalesced_cas": pq["achieved_gatomic_s"] / peaks["coalesced_cas_gops"],
+                "peak_source": "measured live on this GPU: min(coalesced 64-bit CAS rate / slot RMWs per op, "
+                               "2 x 32 x same-address fetch-add rate)"}
+
+    # ---- imbalanced producer / consumer split (capacity 2^16, 2^18 threads, 10^7 ops) ----
+    split = {}
+    if not args.no_sweep:
+        Ts, total, cap = 1 << 18, 10 ** 7, 1 << 16
+        for k in kinds:
+            qs = gq.Queue(k, cap if k != "ymc" else int(1.4 * total), 8, max_threads=Ts)
+            for frac in (0.1, 0.5, 0.9):
+                P = int(frac * Ts)
+                cc = torch.zeros(8, dtype=torch.int64, device=dev)
+                best = None
+                for rep in range(3):
+                    qs.reset()
+                    cc.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    gq.gq_run(qs.handle, gq.GQ_RUN_SPLIT, Ts, producers=P, total_ops=total, counts=cc)
+                    e1.record()
+                    e1.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    if rep and (best is None or ms < best[0]):
+                        best = (ms, cc.cpu().numpy().copy())
+                st = qs.sync_status()
+                assert st == 0, (k, frac, gq.status_str(st))
+                ms, cn = best
+                ok = float(cn[gq.GQ_CNT_ENQ_OK] + cn[gq.GQ_CNT_DEQ_OK])
+                pqk = per_queue[k]
+                ceiling = min(pqk["slot_ceiling_mops"], pqk["counter_ceiling_mops"]) * 1e6
+                # one direction only is busy on its counters when the split is lopsided; the
+                # balanced ceiling is the reference either way
+                split["%s_p%d" % (k, int(frac * 100))] = {
+                    "succ_mops": round(ok / (ms * 1e-3) / 1e6, 1),
+                    "attempted_mops": round(total / (ms * 1e-3) / 1e6, 1), "ms": round(ms, 3),
+                    "enq_ok": int(cn[gq.GQ_CNT_ENQ_OK]), "full": int(cn[gq.GQ_CNT_ENQ_FULL]),
+                    "deq_ok": int(cn[gq.GQ_CNT_DEQ_OK]), "empty": int(cn[gq.GQ_CNT_DEQ_EMPTY]),
+                    "frac_of_binding_ceiling": round(ok / (ms * 1e-3) / ceiling, 4)}
+            qs.close()
 
     # ---- sweep over thread counts (kernel only, untimed region) ----
     sweep = {}
@@ -553,7 +620,7 @@ def main():
     if not args.no_sweep:
         for k in kinds:
             phases[k] = {}
-            for Ts in sorted({1 << 16, T}):
+            for Ts in [1 << lg for lg in range(10, 21) if (1 << lg) <= T]:
                 target = min(CAPACITY, Ts * K)
                 cc = torch.zeros(8, dtype=torch.int64, device=dev)
                 res = {}
@@ -575,48 +642,50 @@ def main():
                 phases[k][str(Ts)] = res
 
     # ---- end to end through the public batch API with host buffers ----
+    # One step: for every queue kind, pinned host -> device copy of 2^20 items,
+    # gq_enqueue_batch, gq_dequeue_batch, device -> host copy of the values and
+    # the counts.  Each kind runs on its own stream, so one kind's copies
+    # overlap another's kernels; the step ends when all streams are done.
     e2e = None
     if not args.no_e2e:
         n = CAPACITY
+        streams = {k: torch.cuda.Stream(device=dev) for k in kinds}
         host_items = torch.arange(1, n + 1, dtype=torch.int64).pin_memory()
-        host_out = torch.empty(n, dtype=torch.int64).pin_memory()
-        host_cnt = torch.empty(2, dtype=torch.int64).pin_memory()
-        d_items = torch.empty(n, dtype=torch.int64, device=dev)
-        d_out = torch.empty(n, dtype=torch.int64, device=dev)
-        d_cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+        bufs = {k: {"out": torch.empty(n, dtype=torch.int64).pin_memory(),
+                    "cnt": torch.empty(2, dtype=torch.int64).pin_memory(),
+                    "d_items": torch.empty(n, dtype=torch.int64, device=dev),
+                    "d_out": torch.empty(n, dtype=torch.int64, device=dev),
+                    "d_cnt": torch.zeros(2, dtype=torch.int64, device=dev)} for k in kinds}
+        torch.cuda.synchronize()
 
         def e2e_step():
             for k in kinds:
-                queues[k].reset()
-                d_items.copy_(host_items, non_blocking=True)
-                gq.gq_enqueue_batch(queues[k].handle, d_items, n, None, d_cnt[0:1])
-                gq.gq_dequeue_batch(queues[k].handle, d_out, n, None, d_cnt[1:2])
-                host_out.copy_(d_out, non_blocking=True)
-                host_cnt.copy_(d_cnt, non_blocking=True)
-            torch.cuda.synchronize()
-            return int(host_cnt[0]) + int(host_cnt[1])
+                b = bufs[k]
+                with torch.cuda.stream(streams[k]):
+                    queues[k].reset()
+                    b["d_items"].copy_(host_items, non_blocking=True)
+                    gq.gq_enqueue_batch(queues[k].handle, b["d_items"], n, None, b["d_cnt"][0:1])
+                    gq.gq_dequeue_batch(queues[k].handle, b["d_out"], n, None, b["d_cnt"][1:2])
+                    b["out"].copy_(b["d_out"], non_blocking=True)
+                    b["cnt"].copy_(b["d_cnt"], non_blocking=True)
+            for k in kinds:
+                streams[k].synchronize()
+            return sum(int(bufs[k]["cnt"][0]) + int(bufs[k]["cnt"][1]) for k in kinds)
 
-        for _ in range(2):
-            e2e_step()
+        for _ in range(3):
+            assert e2e_step() == 2 * n * len(kinds)
         t0 = time.perf_counter()
         tot = 0
         for _ in range(args.steps):
-            ok_total = 0
-            for k in kinds:
-                queues[k].reset()
-                d_items.copy_(host_items, non_blocking=True)
-                gq.gq_enqueue_batch(queues[k].handle, d_items, n, None, d_cnt[0:1])
-                gq.gq_dequeue_batch(queues[k].handle, d_out, n, None, d_cnt[1:2])
-                host_out.copy_(d_out, non_blocking=True)
-                host_cnt.copy_(d_cnt, non_blocking=True)
-                torch.cuda.current_stream().synchronize()
-                ok_total += int(host_cnt[0]) + int(host_cnt[1])
-            tot += ok_total
+            tot += e2e_step()
         dt = time.perf_counter() - t0
+        for k in kinds:
+            assert queues[k].sync_status() == 0
         e2e = {"value": tot / dt / 1e6, "unit": "Mops/s", "h2d_bytes_per_step": 8 * n * len(kinds),
                "d2h_bytes_per_step": (8 * n + 16) * len(kinds),
-               "how": "per queue: reset, pinned H2D of 2^20 items, gq_enqueue_batch, gq_dequeue_batch, "
-                      "D2H of values and counts; wall clock over %d steps" % args.steps}
+               "how": "per queue kind on its own stream: reset, pinned H2D of 2^20 items, gq_enqueue_batch, "
+                      "gq_dequeue_batch, D2H of values and counts; the kinds' streams overlap; wall clock over "
+                      "%d steps" % args.steps}
 
     apps = None
     if not args.no_apps:
@@ -644,6 +713,7 @@ def main():
                            "l2": "flushed between timed steps (256 MiB write); queue state re-initialised inside "
                                  "each step"},
                 "roofline": roofline, "peaks": peaks, "per_queue": per_queue, "sweep": sweep, "phases": phases,
+                "split_2p18_cap2p16": split,
                 "cpu_baseline": cpu, "e2e": e2e, "apps": apps, "batched": batched, "serving": serving,
                 "gpu_launches": args.steps * sum(launches_per_step[k] for k in kinds),
                 "clocks": clocks}

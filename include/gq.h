@@ -57,6 +57,8 @@ typedef enum {
 /* Opaque queue handle. */
 typedef struct gq_queue* gq_handle;
 
+#define GQ_DUE_WAIT_OFF 0xFFFFFFFFu
+
 /* Creation options.  Zero-initialise and set what you need; 0 = default. */
 typedef struct {
     /* Width of the cycle tag in bits.  Default 31 for G-LFQ (slot <Cycle 31 |
@@ -79,7 +81,14 @@ typedef struct {
     /* Back-off: a ring operation whose ticket attempt failed sleeps this many
      * nanoseconds (__nanosleep) before taking the next ticket.  Default 0. */
     uint32_t backoff_ns;
-    uint32_t reserved_opt;
+    /* Due-install wait of the ring queues (G-LFQ, G-WFQ): a dequeuer whose
+     * slot still holds an older cycle's empty entry while Tail is already past
+     * its ticket (the enqueuer holding that ticket is about to install)
+     * re-reads the slot up to this many times, about 32 ns apart, before
+     * ruling it out.  0 = default: no waiting (the plain TryDeq of
+     * Algorithm 1; waiting measured no better on the benchmark workloads);
+     * GQ_DUE_WAIT_OFF = no waiting either.  At most 65536. */
+    uint32_t due_wait;
     /* Initial value of every ticket counter (tests of counter wrap-around).
      * Must be a multiple of 2 * capacity.  Default 0. */
     uint64_t start_ticket;
@@ -106,7 +115,7 @@ typedef struct {
     uint32_t batch_width;           /* WaveFAA group width                          */
     uint32_t ring_order;            /* log2(2n)                                    */
     uint32_t backoff_ns;            /* sleep after a failed ticket attempt          */
-    uint32_t reserved1;
+    uint32_t due_wait;              /* due-install polls of a ring dequeuer (0: none) */
     uint64_t capacity;              /* ring: n; YMC: pool cells                    */
     uint64_t slot_mask;             /* 2n - 1                                      */
     uint64_t cycle_mask;            /* R - 1, R = 2^cycle_bits                     */

@@ -55,6 +55,27 @@ enum {
     GQ_CNT_RESERVED = 7
 };
 
+/* Event counters of the counting kernels (gq_run / gq_run_multi with
+ * d_opcount), summed over all operations.  They measure what each successful
+ * operation costs in L2 atomics against the algorithmic count (Section III-B:
+ * one slot CAS per ring operation and one counter fetch-add per warp batch).
+ * Slow-path internals are not included (gq_get_stats counts those). */
+enum {
+    GQ_OC_TICKETS = 0,    /* tickets taken (per lane)                                     */
+    GQ_OC_FAA = 1,        /* counter fetch-and-adds issued (one per WaveFAA batch)        */
+    GQ_OC_CAS = 2,        /* CAS attempts on slots / cells: install, repair, consume, claim */
+    GQ_OC_CAS_FAIL = 3,   /* ... of which failed                                          */
+    GQ_OC_RMW = 4,        /* other slot RMWs (Consume's atomic-OR fallback)               */
+    GQ_OC_THRESHOLD = 5,  /* Threshold RMWs (reset, decrement; one per group of lanes)     */
+    GQ_OC_CATCHUP = 6,    /* Tail catch-ups of EMPTY dequeues (one per group of lanes)     */
+    GQ_OC_BURNED = 7,     /* tickets given up without an install or an item (RETRY/EMPTY) */
+    GQ_OC_LOADS = 8,      /* first loads of a ticket's slot or cell                        */
+    GQ_OC_SLOW = 9,       /* slow-path requests (G-WFQ, G-WFQ-YMC)                          */
+    GQ_OC_SPIN = 10,      /* further reads of an empty slot / cell whose enqueuer is due     */
+    GQ_OC_MARKED = 11,    /* G-WFQ-YMC: cells marked unusable by a dequeuer                 */
+    GQ_OC_N = 12
+};
+
 typedef struct {
     uint32_t mode;            /* GQ_RUN_*                                                  */
     uint32_t threads;         /* logical threads (one device thread each)                 */
@@ -77,6 +98,10 @@ typedef struct {
                               /* the same ticket, and of two enqueues (dequeues) that do */
                               /* not overlap in time the earlier has the smaller one.    */
                               /* Non-null selects a separate recording kernel.           */
+    unsigned long long* d_opcount; /* nullable, GQ_OC_N words, added to: event counts of   */
+                              /* every operation's fast path (GQ_OC_*).  Non-null selects */
+                              /* a separate counting kernel (never the timed one); not   */
+                              /* combinable with d_ticket.                               */
 } gq_run_args;
 
 /* Launches the driver kernel.  For SPLIT, ops
@@ -139,8 +164,10 @@ int gq_wavefaa_probe(const uint8_t* d_take, uint32_t threads, uint32_t width, un
  * view, the WaveFAA batch width (if non-zero), the back-off, when
  * tune->patience_set is 1 G-WFQ's patience, and when tune->help_delay is
  * non-zero G-WFQ's help delay D (GQ_ERR_TOO_MANY_THREADS if some queue would
- * leave its cycle-tag bound R > D k / n + 6); this is how the autotuner tries
- * settings without recreating queues.  Asynchronous on `stream`. */
+ * leave its cycle-tag bound R > D k / n + 6), and when tune->due_wait is
+ * non-zero the ring queues' due-install wait (GQ_DUE_WAIT_OFF: none); this is
+ * how the autotuner tries settings without recreating queues.  Asynchronous on
+ * `stream`. */
 int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void* d_views, const gq_options* tune,
                      void* stream);
 
@@ -154,6 +181,17 @@ typedef struct {
     uint32_t reserved;
     uint64_t ops_per_queue;        /* split evenly over the queue's threads                */
     unsigned long long* d_counts;  /* 8 words, added to (GQ_CNT_* layout)                  */
+    /* Recorder (nullable; d_ticket non-null selects a separate recording kernel
+     * and then needs d_status and d_val): op i of logical thread t of queue q
+     * goes to entry (q * K + i) * threads_per_queue + t with
+     * K = ceil(ops_per_queue / threads_per_queue): its status, its value (the
+     * enqueued token, or the dequeued value, 0 if none) and its ticket (as in
+     * gq_run_args.d_ticket).  Entries of ops a thread does not run are left
+     * untouched. */
+    int8_t* d_status;
+    uint64_t* d_val;
+    uint64_t* d_ticket;
+    unsigned long long* d_opcount; /* nullable, GQ_OC_N words: counting kernel (as gq_run) */
 } gq_multi_args;
 
 /* Producer/consumer split workload on every queue of d_views at once: logical

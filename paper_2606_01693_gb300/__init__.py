@@ -27,10 +27,15 @@ GQ_OK, GQ_FULL, GQ_EMPTY = 0, 1, 2
 GQ_ERR_INVALID, GQ_ERR_NOMEM, GQ_ERR_CUDA, GQ_ERR_TIMEOUT = -1, -2, -3, -4
 GQ_ERR_POOL_EXHAUSTED, GQ_ERR_TOO_MANY_THREADS, GQ_ERR_RESERVED_VALUE = -5, -6, -7
 GQ_RUN_PAIRS, GQ_RUN_MIXED, GQ_RUN_SPLIT = 0, 1, 2
+GQ_DUE_WAIT_OFF = 0xFFFFFFFF
 GQ_PEAK_SAME_ADDR_FAA, GQ_PEAK_COALESCED_CAS, GQ_PEAK_SCATTERED_CAS, GQ_PEAK_COALESCED_LOAD = 0, 1, 2, 3
 GQ_PEAK_SPREAD_FAA, GQ_PEAK_PACKED_FAA = 4, 5
 (GQ_CNT_ENQ_OK, GQ_CNT_ENQ_FULL, GQ_CNT_DEQ_OK, GQ_CNT_DEQ_EMPTY, GQ_CNT_SUM_ENQ, GQ_CNT_SUM_DEQ,
  GQ_CNT_ERRORS) = range(7)
+# event counters of the counting kernels (gq_run / gq_run_multi with opcount=)
+OC_NAMES = ["tickets", "faa", "cas", "cas_fail", "rmw", "threshold", "catchup", "burned", "loads", "slow",
+            "spin", "marked"]
+GQ_OC_N = len(OC_NAMES)
 
 # Every symbol the headers in include/ declare.
 EXPORTS = [
@@ -53,7 +58,7 @@ class gq_options(ctypes.Structure):
     _fields_ = [("cycle_bits", ctypes.c_uint32), ("patience_enq", ctypes.c_uint32),
                 ("patience_deq", ctypes.c_uint32), ("patience_set", ctypes.c_uint32),
                 ("help_delay", ctypes.c_uint32), ("batch_width", ctypes.c_uint32),
-                ("backoff_ns", ctypes.c_uint32), ("reserved_opt", ctypes.c_uint32),
+                ("backoff_ns", ctypes.c_uint32), ("due_wait", ctypes.c_uint32),
                 ("start_ticket", ctypes.c_uint64)]
 
 
@@ -62,7 +67,7 @@ class gq_run_args(ctypes.Structure):
                 ("ops", ctypes.c_uint32), ("producers", ctypes.c_uint32), ("delay_ns", ctypes.c_uint32),
                 ("total_ops", ctypes.c_uint64), ("d_sched", ctypes.c_void_p), ("d_status", ctypes.c_void_p),
                 ("d_val", ctypes.c_void_p), ("d_call", ctypes.c_void_p), ("d_end", ctypes.c_void_p),
-                ("d_counts", ctypes.c_void_p), ("d_ticket", ctypes.c_void_p)]
+                ("d_counts", ctypes.c_void_p), ("d_ticket", ctypes.c_void_p), ("d_opcount", ctypes.c_void_p)]
 
 
 _lib = None
@@ -235,9 +240,11 @@ def gq_info(h: int) -> tuple[int, bool]:
 
 def gq_run(h: int, mode: int, threads: int, block: int = 256, ops: int = 0, producers: int = 0,
            total_ops: int = 0, sched=None, status=None, val=None, call=None, end=None, counts=None,
-           delay_ns: int = 0, stream=None, ticket=None) -> None:
+           delay_ns: int = 0, stream=None, ticket=None, opcount=None) -> None:
+    _need(opcount, GQ_OC_N, 8, "gq_run: opcount")
+    _need(counts, 8, 8, "gq_run: counts")
     a = gq_run_args(mode, threads, block, ops, producers, delay_ns, total_ops, _ptr(sched), _ptr(status),
-                    _ptr(val), _ptr(call), _ptr(end), _ptr(counts), _ptr(ticket))
+                    _ptr(val), _ptr(call), _ptr(end), _ptr(counts), _ptr(ticket), _ptr(opcount))
     _check(load().gq_run(h, ctypes.byref(a), _stream(stream)), "gq_run")
 
 
@@ -334,7 +341,8 @@ class gq_multi_args(ctypes.Structure):
     _fields_ = [("nqueues", ctypes.c_uint32), ("threads_per_queue", ctypes.c_uint32),
                 ("producers_per_queue", ctypes.c_uint32), ("block", ctypes.c_uint32), ("blocks", ctypes.c_uint32),
                 ("kind", ctypes.c_uint32), ("elem_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
-                ("ops_per_queue", ctypes.c_uint64), ("d_counts", ctypes.c_void_p)]
+                ("ops_per_queue", ctypes.c_uint64), ("d_counts", ctypes.c_void_p), ("d_status", ctypes.c_void_p),
+                ("d_val", ctypes.c_void_p), ("d_ticket", ctypes.c_void_p), ("d_opcount", ctypes.c_void_p)]
 
 
 def gq_multi_prepare(handles, views, tune: gq_options | None = None, stream=None) -> None:
@@ -344,9 +352,20 @@ def gq_multi_prepare(handles, views, tune: gq_options | None = None, stream=None
 
 
 def gq_run_multi(views, nqueues: int, kind: int, elem_bytes: int, threads_per_queue: int, producers_per_queue: int,
-                 ops_per_queue: int, counts, block: int = 256, blocks: int = 0, stream=None) -> None:
+                 ops_per_queue: int, counts, block: int = 256, blocks: int = 0, stream=None, status=None, val=None,
+                 ticket=None, opcount=None) -> None:
+    """Producer/consumer workload on every queue of `views` in one persistent launch.  status / val /
+    ticket (recorder) hold nqueues * K * threads_per_queue entries, K = ceil(ops_per_queue /
+    threads_per_queue); opcount (GQ_OC_N words) selects the counting kernel."""
+    K = -(-ops_per_queue // threads_per_queue)
+    n = nqueues * K * threads_per_queue
+    _need(counts, 8, 8, "gq_run_multi: counts")
+    _need(status, n, 1, "gq_run_multi: status")
+    _need(val, n, 8, "gq_run_multi: val")
+    _need(ticket, n, 8, "gq_run_multi: ticket")
+    _need(opcount, GQ_OC_N, 8, "gq_run_multi: opcount")
     a = gq_multi_args(nqueues, threads_per_queue, producers_per_queue, block, blocks, kind, elem_bytes, 0,
-                      ops_per_queue, _ptr(counts))
+                      ops_per_queue, _ptr(counts), _ptr(status), _ptr(val), _ptr(ticket), _ptr(opcount))
     _check(load().gq_run_multi(_ptr(views), ctypes.byref(a), _stream(stream)), "gq_run_multi")
 
 
@@ -363,10 +382,11 @@ class MultiQueue:
         self.prepare()
 
     def prepare(self, batch_width: int = 0, backoff_ns: int | None = None, patience=None, help_delay: int = 0,
-                stream=None):
+                due_wait: int = 0, stream=None):
         tune = None
-        if batch_width or backoff_ns is not None or patience is not None or help_delay:
-            tune = gq_options(batch_width=batch_width, backoff_ns=backoff_ns or 0, help_delay=help_delay)
+        if batch_width or backoff_ns is not None or patience is not None or help_delay or due_wait:
+            tune = gq_options(batch_width=batch_width, backoff_ns=backoff_ns or 0, help_delay=help_delay,
+                              due_wait=due_wait)
             if patience is not None:
                 tune.patience_enq, tune.patience_deq, tune.patience_set = patience[0], patience[1], 1
         gq_multi_prepare(self.handles, self.views, tune, stream)
@@ -375,9 +395,11 @@ class MultiQueue:
         for q in self.queues:
             q.reset(stream)
 
-    def run(self, threads_per_queue, producers_per_queue, ops_per_queue, counts, block=256, blocks=0, stream=None):
+    def run(self, threads_per_queue, producers_per_queue, ops_per_queue, counts, block=256, blocks=0, stream=None,
+            **record):
+        """record: status= / val= / ticket= (recorder) or opcount= (counting kernel), see gq_run_multi."""
         gq_run_multi(self.views, len(self.queues), self.kind, self.elem_bytes, threads_per_queue, producers_per_queue,
-                     ops_per_queue, counts, block, blocks, stream)
+                     ops_per_queue, counts, block, blocks, stream, **record)
 
     def run_per_call(self, threads_per_queue, producers_per_queue, ops_per_queue, counts, block=256, stream=None):
         """The plain form: one split-workload launch per queue, one after another."""

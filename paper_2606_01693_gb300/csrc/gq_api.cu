@@ -33,6 +33,9 @@ int resolve(int kind, uint64_t cap, uint32_t elem, uint32_t max_threads, const g
     if (o.batch_width == 0) o.batch_width = 32;
     if (!is_pow2(o.batch_width) || o.batch_width > 32) return GQ_ERR_INVALID;
     if (o.backoff_ns > 1000000) return GQ_ERR_INVALID;
+    if (o.due_wait == GQ_DUE_WAIT_OFF) o.due_wait = 0;
+    else if (o.due_wait > 65536) return GQ_ERR_INVALID;
+    if (kind == GQ_YMC) o.due_wait = 0;
     if (kind == GQ_YMC) {
         if (cap < 2 || cap > (1ull << 40)) return GQ_ERR_INVALID;
         if (max_threads > (1u << 24) - 1) return GQ_ERR_TOO_MANY_THREADS;   // 24-bit thread field of cell references
@@ -328,6 +331,7 @@ extern "C" int gq_create(int kind, uint64_t capacity, uint32_t elem_bytes, uint3
     d.help_delay = o.help_delay;
     d.batch_width = o.batch_width;
     d.backoff_ns = o.backoff_ns;
+    d.due_wait = o.due_wait;
     d.capacity = capacity;
     if (kind != GQ_YMC) {
         d.ring_order = d.log2n + 1;

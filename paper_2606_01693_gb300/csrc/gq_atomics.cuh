@@ -82,14 +82,57 @@ __device__ __forceinline__ u64 globaltimer() {
 // many lanes, each batching on its own (width 1 = one atomic per thread).
 // MATCH groups lanes by counter address first (__match_any_sync), for callers
 // whose lanes may target different queues.
-template <bool MATCH = false>
+// ---- operation counters (counting instantiations only) ---------------------
+// Kernels instantiated with CNT = true count the events of each operation's
+// fast path per thread in shared memory (one column per thread of the block;
+// a thread only touches its own entries, so plain increments suffice) and sum
+// them per warp at the end.  Kernels instantiated with CNT = false -- every
+// timed kernel -- contain none of it.  Event kinds (GQ_OC_* in gq_drivers.h):
+enum : int {
+    kOcTicket = 0,   // tickets taken (one per lane per counter reservation)
+    kOcFaa = 1,      // counter fetch-and-adds issued (one per WaveFAA batch)
+    kOcCas = 2,      // CAS attempts on slots / cells (install, repair, consume, claim)
+    kOcCasFail = 3,  // ... of which failed
+    kOcRmw = 4,      // other slot RMWs (the atomic-OR fallback of Consume)
+    kOcThr = 5,      // Threshold RMWs (reset exchange, decrement)
+    kOcCatch = 6,    // catch-up operations on Tail / T / H
+    kOcBurn = 7,     // tickets given up without an install or an item (RETRY, EMPTY)
+    kOcLoad = 8,     // slot / cell loads (first read of the ticket's slot or cell)
+    kOcSlow = 9,     // slow-path requests (G-WFQ, G-WFQ-YMC)
+    kOcSpin = 10,    // further reads of an empty slot / cell while its enqueuer is due
+    kOcMark = 11,    // G-WFQ-YMC: cells marked unusable by a dequeuer
+    kOcN = 12
+};
+constexpr int kOcMaxBlock = 256;
+
+__device__ __forceinline__ u32* oc_table() {
+    __shared__ u32 s_oc[kOcN * kOcMaxBlock];
+    return s_oc;
+}
+template <bool CNT>
+__device__ __forceinline__ void oc_add(int what, u32 n = 1) {
+    if constexpr (CNT) oc_table()[what * kOcMaxBlock + threadIdx.x] += n;
+}
+template <bool CNT>
+__device__ __forceinline__ void oc_cas(bool ok) {
+    if constexpr (CNT) {
+        oc_table()[kOcCas * kOcMaxBlock + threadIdx.x] += 1;
+        if (!ok) oc_table()[kOcCasFail * kOcMaxBlock + threadIdx.x] += 1;
+    }
+}
+
+template <bool MATCH = false, bool CNT = false>
 __device__ __forceinline__ u64 warp_faa(u64* ctr, u64 step, u32 width = 32) {
     u32 mask = __activemask();
     if (MATCH) mask = __match_any_sync(mask, reinterpret_cast<u64>(ctr));
     if (width < 32) mask &= ((1u << width) - 1u) << (lane_id() & ~(width - 1u));
     const u32 leader = __ffs(mask) - 1;
     u64 base = 0;
-    if (lane_id() == leader) base = faa_rlx(ctr, step * (u64)__popc(mask));
+    oc_add<CNT>(kOcTicket);
+    if (lane_id() == leader) {
+        oc_add<CNT>(kOcFaa);
+        base = faa_rlx(ctr, step * (u64)__popc(mask));
+    }
     base = __shfl_sync(mask, base, leader);
     return base + step * (u64)__popc(mask & lanemask_lt());
 }
@@ -114,6 +157,29 @@ __device__ __forceinline__ void warp_add_full(unsigned long long* dst, u64 v) {
     __syncwarp();
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane_id() == 0 && v) atomicAdd(dst, v);
+}
+
+// Counting kernels: zero this thread's counters at the start, add the warp's
+// sums to dst[0 .. kOcN) at the end.  Every thread of the block calls both, and
+// blocks are whole warps.  The end first gathers all 32 lanes (__syncwarp), so
+// the reductions run in lockstep: lanes that arrive at different times must not
+// meet in one reduction at different counters (warp_add_full inside a loop
+// could: its active-mask test sees lanes of different iterations at one PC).
+template <bool CNT>
+__device__ __forceinline__ void oc_begin() {
+    if constexpr (CNT)
+        for (int k = 0; k < kOcN; ++k) oc_table()[k * kOcMaxBlock + threadIdx.x] = 0;
+}
+template <bool CNT>
+__device__ __forceinline__ void oc_end(unsigned long long* dst) {
+    if constexpr (CNT) {
+        __syncwarp();
+        for (int k = 0; k < kOcN; ++k) {
+            u64 v = oc_table()[k * kOcMaxBlock + threadIdx.x];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane_id() == 0 && v) atomicAdd(dst + k, v);
+        }
+    }
 }
 
 }  // namespace gqd

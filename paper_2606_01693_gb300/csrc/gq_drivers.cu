@@ -15,6 +15,8 @@ static_assert(sizeof(gq_dev) <= GQ_VIEW_BYTES, "gq_dev must fit GQ_VIEW_BYTES");
 
 namespace {
 
+constexpr int kOcStaticBytes = kOcN * kOcMaxBlock * (int)sizeof(u32);
+
 struct RunK {
     u32 mode, threads, ops, producers, delay_ns;
     u64 total_ops;
@@ -25,6 +27,7 @@ struct RunK {
     u64* end;
     unsigned long long* counts;
     u64* ticket;
+    unsigned long long* opcnt;
 };
 
 __device__ __forceinline__ u32 mix32(u32 a, u32 b) {
@@ -37,11 +40,13 @@ __device__ __forceinline__ u32 mix32(u32 a, u32 b) {
 
 // 256 threads x 4 blocks per SM caps registers at 64: the rarely taken slow
 // paths of G-WFQ / G-WFQ-YMC may spill instead of halving occupancy.
-// REC: also record each successful operation's ticket (a.ticket); a separate
-// instantiation, so the timed kernels carry none of it.
-template <class T, int KIND, bool REC>
+// REC: also record each successful operation's ticket (a.ticket); CNT: count
+// the events of every operation (a.opcnt, see gq_atomics.cuh).  Both are
+// separate instantiations, so the timed kernels carry none of it.
+template <class T, int KIND, bool REC, bool CNT>
 __global__ void __launch_bounds__(256, 4) k_run(const __grid_constant__ gq_dev q, const __grid_constant__ RunK a) {
     const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
+    oc_begin<CNT>();
     u32 c_enq_ok = 0, c_full = 0, c_deq_ok = 0, c_empty = 0, c_err = 0;   // per-thread counts
     u64 s_enq = 0, s_deq = 0;
     if (t < a.threads) {
@@ -73,13 +78,13 @@ __global__ void __launch_bounds__(256, 4) k_run(const __grid_constant__ gq_dev q
                 if (is_enq) {
                     v = (sizeof(T) == 4) ? (((u64)t << 16) | seq) : (((u64)t << 32) | (u64)(seq + 1));
                     ++seq;
-                    s = queue_enqueue<T, KIND>(q, (T)v, t, tkp);
+                    s = queue_enqueue<T, KIND, false, CNT>(q, (T)v, t, tkp);
                     if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
                     else if (s == GQ_FULL) ++c_full;
                     else ++c_err;
                 } else {
                     T x = 0;
-                    s = queue_dequeue<T, KIND>(q, &x, t, tkp);
+                    s = queue_dequeue<T, KIND, false, CNT>(q, &x, t, tkp);
                     v = (s == GQ_OK) ? (u64)x : 0;
                     if (s == GQ_OK) { ++c_deq_ok; s_deq += v; }
                     else if (s == GQ_EMPTY) ++c_empty;
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(256, 4) k_run(const __grid_constant__ gq_dev q
                     ++seq;
                 }
                 T x = (T)v;
-                s = queue_op<T, KIND>(q, is_enq, &x, t, tkp);
+                s = queue_op<T, KIND, CNT>(q, is_enq, &x, t, tkp);
                 if (is_enq) {
                     if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
                     else if (s == GQ_FULL) ++c_full;
@@ -119,6 +124,7 @@ __global__ void __launch_bounds__(256, 4) k_run(const __grid_constant__ gq_dev q
     warp_add_full(&a.counts[GQ_CNT_SUM_ENQ], s_enq);
     warp_add_full(&a.counts[GQ_CNT_SUM_DEQ], s_deq);
     warp_add_full(&a.counts[GQ_CNT_ERRORS], c_err);
+    oc_end<CNT>(a.opcnt);
 }
 
 template <class T, int KIND>
@@ -152,7 +158,7 @@ __global__ void k_drain(const __grid_constant__ gq_dev q, u64* out, u64 max, uns
     *count = k;
 }
 
-template <class T, int KIND, bool REC>
+template <class T, int KIND, bool REC, bool CNT>
 int launch_run(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
     const u32 grid = (a.threads + block - 1) / block;
     // G-LFQ on a grid of at least two waves at 768 threads per SM: reserve
@@ -169,30 +175,36 @@ int launch_run(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
             // per_sm blocks fit, one more does not
             const int sm_bytes = h->smem_per_sm;
             const int foot = (sm_bytes / (int)per_sm + sm_bytes / (int)(per_sm + 1)) / 2;
-            smem = (size_t)std::min(std::max(foot - h->smem_reserved, 0), h->smem_optin);
+            const int stat = CNT ? kOcStaticBytes : 0;     // the counting kernel's static table
+            smem = (size_t)std::min(std::max(foot - h->smem_reserved - stat, 0), h->smem_optin - stat);
         }
     }
-    k_run<T, KIND, REC><<<grid, block, smem, st>>>(h->dev, a);
+    k_run<T, KIND, REC, CNT><<<grid, block, smem, st>>>(h->dev, a);
     return gq_check_launch();
 }
 
-template <class T, bool REC>
+template <class T, bool REC, bool CNT>
 cudaError_t allow_run_smem(int bytes) {
-    return cudaFuncSetAttribute(k_run<T, GQ_LFQ, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    // static shared memory (the counting kernel's table) counts against the same per-block limit
+    const int stat = CNT ? kOcStaticBytes : 0;
+    return cudaFuncSetAttribute(k_run<T, GQ_LFQ, REC, CNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes - stat);
 }
 
-template <class T, bool REC>
+template <class T, bool REC, bool CNT>
 int dispatch_run_rec(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
     switch (h->dev.kind) {
-        case GQ_LFQ: return launch_run<T, GQ_LFQ, REC>(h, a, block, st);
-        case GQ_WFQ: return launch_run<T, GQ_WFQ, REC>(h, a, block, st);
-        default: return launch_run<T, GQ_YMC, REC>(h, a, block, st);
+        case GQ_LFQ: return launch_run<T, GQ_LFQ, REC, CNT>(h, a, block, st);
+        case GQ_WFQ: return launch_run<T, GQ_WFQ, REC, CNT>(h, a, block, st);
+        default: return launch_run<T, GQ_YMC, REC, CNT>(h, a, block, st);
     }
 }
 
 template <class T>
 int dispatch_run(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
-    return a.ticket ? dispatch_run_rec<T, true>(h, a, block, st) : dispatch_run_rec<T, false>(h, a, block, st);
+    if (a.opcnt) return dispatch_run_rec<T, false, true>(h, a, block, st);
+    return a.ticket ? dispatch_run_rec<T, true, false>(h, a, block, st)
+                    : dispatch_run_rec<T, false, false>(h, a, block, st);
 }
 
 template <class T>
@@ -217,36 +229,62 @@ int dispatch_drain(gq_queue* h, u64* out, u64 max, unsigned long long* count, cu
 }
 
 struct MultiK {
-    u32 nq, tpq, ppq;
+    u32 nq, tpq, ppq, kmax;
     u64 opq;
     unsigned long long* counts;
+    int8_t* status;
+    u64* val;
+    u64* ticket;
+    unsigned long long* opcnt;
 };
 
-template <class T, int KIND>
+// REC: record each operation's status, value and ticket at entry
+// ((queue * kmax) + op) * tpq + thread; CNT: count events (a.opcnt).  Both are
+// separate instantiations of the timed kernel.
+// The lanes of one warp may work on different queues at the same time (a lane
+// whose logical thread finished early moves on to the next queue while the
+// others still run), so WaveFAA groups lanes by counter address (MATCH): one
+// fetch-and-add must never hand one queue's tickets to another queue's lanes.
+template <class T, int KIND, bool REC, bool CNT>
 __global__ void __launch_bounds__(256, 4) k_run_multi(const gq_dev* __restrict__ views, const __grid_constant__ MultiK a) {
     const u64 total = (u64)a.nq * a.tpq;
     const u64 stride = (u64)gridDim.x * blockDim.x;
+    oc_begin<CNT>();
     u32 c_enq_ok = 0, c_full = 0, c_deq_ok = 0, c_empty = 0, c_err = 0;
     u64 s_enq = 0, s_deq = 0;
     for (u64 L = (u64)blockIdx.x * blockDim.x + threadIdx.x; L < total; L += stride) {
         const u32 qi = (u32)(L / a.tpq), t = (u32)(L % a.tpq);
         const gq_dev& q = views[qi];
         const u32 nops = (u32)(a.opq / a.tpq) + (t < (u32)(a.opq % a.tpq) ? 1u : 0u);
+        u64 tk = ~0ull;
+        u64* const tkp = REC ? &tk : nullptr;
         if (t < a.ppq) {
             for (u32 i = 0; i < nops; ++i) {
                 const u64 v = (sizeof(T) == 4) ? ((L << 16) | i) : ((L << 32) | (u64)(i + 1));
-                const int s = queue_enqueue<T, KIND>(q, (T)v, t);
+                const int s = queue_enqueue<T, KIND, true, CNT>(q, (T)v, t, tkp);
                 if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
                 else if (s == GQ_FULL) ++c_full;
                 else ++c_err;
+                if constexpr (REC) {
+                    const u64 j = ((u64)qi * a.kmax + i) * a.tpq + t;
+                    a.status[j] = (int8_t)s;
+                    a.val[j] = v;
+                    a.ticket[j] = (s == GQ_OK) ? tk : ~0ull;
+                }
             }
         } else {
             for (u32 i = 0; i < nops; ++i) {
                 T x = 0;
-                const int s = queue_dequeue<T, KIND>(q, &x, t);
+                const int s = queue_dequeue<T, KIND, true, CNT>(q, &x, t, tkp);
                 if (s == GQ_OK) { ++c_deq_ok; s_deq += (u64)x; }
                 else if (s == GQ_EMPTY) ++c_empty;
                 else ++c_err;
+                if constexpr (REC) {
+                    const u64 j = ((u64)qi * a.kmax + i) * a.tpq + t;
+                    a.status[j] = (int8_t)s;
+                    a.val[j] = (s == GQ_OK) ? (u64)x : 0;
+                    a.ticket[j] = (s == GQ_OK) ? tk : ~0ull;
+                }
             }
         }
     }
@@ -257,28 +295,47 @@ __global__ void __launch_bounds__(256, 4) k_run_multi(const gq_dev* __restrict__
     warp_add_full(&a.counts[GQ_CNT_SUM_ENQ], s_enq);
     warp_add_full(&a.counts[GQ_CNT_SUM_DEQ], s_deq);
     warp_add_full(&a.counts[GQ_CNT_ERRORS], c_err);
+    oc_end<CNT>(a.opcnt);
 }
 
-template <class T, int KIND>
-int launch_multi(const gq_dev* views, const gq_multi_args& g, cudaStream_t st) {
-    MultiK a{g.nqueues, g.threads_per_queue, g.producers_per_queue, g.ops_per_queue, g.d_counts};
+template <class T, int KIND, bool REC, bool CNT>
+int launch_multi_k(const gq_dev* views, const gq_multi_args& g, cudaStream_t st) {
+    MultiK a;
+    a.nq = g.nqueues;
+    a.tpq = g.threads_per_queue;
+    a.ppq = g.producers_per_queue;
+    a.kmax = (uint32_t)((g.ops_per_queue + g.threads_per_queue - 1) / g.threads_per_queue);
+    a.opq = g.ops_per_queue;
+    a.counts = g.d_counts;
+    a.status = g.d_status;
+    a.val = reinterpret_cast<u64*>(g.d_val);
+    a.ticket = reinterpret_cast<u64*>(g.d_ticket);
+    a.opcnt = g.d_opcount;
     uint32_t blocks = g.blocks;
     const uint64_t need = ((uint64_t)g.nqueues * g.threads_per_queue + g.block - 1) / g.block;
     if (blocks == 0) {
         int dev = 0, sms = 0, occ = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_run_multi<T, KIND>, (int)g.block, 0) != cudaSuccess)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_run_multi<T, KIND, REC, CNT>, (int)g.block, 0) !=
+                cudaSuccess)
             return GQ_ERR_CUDA;
         blocks = (uint32_t)(occ > 0 ? occ : 1) * (uint32_t)sms;
     }
     if (blocks > need) blocks = (uint32_t)need;
-    k_run_multi<T, KIND><<<blocks, g.block, 0, st>>>(views, a);
+    k_run_multi<T, KIND, REC, CNT><<<blocks, g.block, 0, st>>>(views, a);
     return gq_check_launch();
 }
 
+template <class T, int KIND>
+int launch_multi(const gq_dev* views, const gq_multi_args& g, cudaStream_t st) {
+    if (g.d_opcount) return launch_multi_k<T, KIND, false, true>(views, g, st);
+    if (g.d_ticket) return launch_multi_k<T, KIND, true, false>(views, g, st);
+    return launch_multi_k<T, KIND, false, false>(views, g, st);
+}
+
 __global__ void k_multi_tune(gq_dev* views, u32 n, u32 width, u32 backoff, u32 set_patience, u32 pe, u32 pd,
-                             u32 delay) {
+                             u32 delay, u32 due) {
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (width) views[i].batch_width = width;
@@ -288,6 +345,8 @@ __global__ void k_multi_tune(gq_dev* views, u32 n, u32 width, u32 backoff, u32 s
         views[i].patience_deq = pd;
     }
     if (delay && views[i].kind == GQ_WFQ) views[i].help_delay = delay;
+    // due-install wait: 0 keeps the queue's own, GQ_DUE_WAIT_OFF turns it off
+    if (due && views[i].kind != GQ_YMC) views[i].due_wait = (due == GQ_DUE_WAIT_OFF) ? 0u : due;
 }
 
 }  // namespace
@@ -301,6 +360,7 @@ extern "C" int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void*
             return GQ_ERR_INVALID;
     if (tune && tune->batch_width && (tune->batch_width > 32 || (tune->batch_width & (tune->batch_width - 1))))
         return GQ_ERR_INVALID;
+    if (tune && tune->due_wait > 65536 && tune->due_wait != GQ_DUE_WAIT_OFF) return GQ_ERR_INVALID;
     // a new G-WFQ help delay D must keep every queue within its modular-cycle bound R > D k / n + 6
     if (tune && tune->help_delay && queues[0]->dev.kind == GQ_WFQ)
         for (uint32_t i = 0; i < nqueues; ++i) {
@@ -317,7 +377,7 @@ extern "C" int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void*
     if (tune) {
         k_multi_tune<<<(nqueues + 255) / 256, 256, 0, st>>>(v, nqueues, tune->batch_width, tune->backoff_ns,
                                                             tune->patience_set, tune->patience_enq, tune->patience_deq,
-                                                            tune->help_delay);
+                                                            tune->help_delay, tune->due_wait);
         return gq_check_launch();
     }
     return GQ_OK;
@@ -332,6 +392,8 @@ extern "C" int gq_run_multi(const void* d_views, const gq_multi_args* args, void
     if (g.elem_bytes == 4 && ((uint64_t)g.nqueues * g.threads_per_queue > 65536 ||
                               g.ops_per_queue / g.threads_per_queue >= 65536))
         return GQ_ERR_INVALID;
+    if (g.d_ticket && (!g.d_status || !g.d_val || g.d_opcount)) return GQ_ERR_INVALID;
+    if (g.ops_per_queue / g.threads_per_queue >= (1ull << 32)) return GQ_ERR_INVALID;
     const gq_dev* v = static_cast<const gq_dev*>(d_views);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (g.elem_bytes == 4) {
@@ -351,10 +413,12 @@ extern "C" int gq_run_multi(const void* d_views, const gq_multi_args* args, void
 int gq_run_kernels_init(int device, int smem_optin) {
     static std::atomic<int> done[64];
     if (device >= 0 && device < 64 && done[device].load(std::memory_order_acquire)) return GQ_OK;
-    if (allow_run_smem<unsigned int, false>(smem_optin) != cudaSuccess ||
-        allow_run_smem<unsigned int, true>(smem_optin) != cudaSuccess ||
-        allow_run_smem<unsigned long long, false>(smem_optin) != cudaSuccess ||
-        allow_run_smem<unsigned long long, true>(smem_optin) != cudaSuccess) {
+    if (allow_run_smem<unsigned int, false, false>(smem_optin) != cudaSuccess ||
+        allow_run_smem<unsigned int, true, false>(smem_optin) != cudaSuccess ||
+        allow_run_smem<unsigned int, false, true>(smem_optin) != cudaSuccess ||
+        allow_run_smem<unsigned long long, false, false>(smem_optin) != cudaSuccess ||
+        allow_run_smem<unsigned long long, true, false>(smem_optin) != cudaSuccess ||
+        allow_run_smem<unsigned long long, false, true>(smem_optin) != cudaSuccess) {
         cudaGetLastError();
         return GQ_ERR_CUDA;
     }
@@ -390,6 +454,8 @@ extern "C" int gq_run(gq_handle h, const gq_run_args* args, void* stream) {
     a.end = reinterpret_cast<u64*>(g.d_end);
     a.counts = g.d_counts;
     a.ticket = reinterpret_cast<u64*>(g.d_ticket);
+    a.opcnt = g.d_opcount;
+    if (a.ticket && a.opcnt) return GQ_ERR_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return h->dev.elem_bytes == 4 ? dispatch_run<unsigned int>(h, a, g.block, st)
                                   : dispatch_run<unsigned long long>(h, a, g.block, st);

@@ -80,18 +80,108 @@ __device__ __forceinline__ void ring_catchup(const gq_ring_view& r, u64 head) {
     atomicMax(reinterpret_cast<unsigned long long*>(r.tail), head);
 }
 
+// ---- warp-aggregated updates of the hot Threshold and Tail words -----------
+// In near-empty and near-full rings most ring operations end on the Threshold
+// word (a decrement per failed dequeue, a reset per install that finds it
+// changed), all on one address per ring: at one RMW per lane those serialise
+// at the single-address rate.  The converged lanes that update the same word
+// do it with one RMW, as WaveFAA does for tickets, and every lane sees the
+// outcome its own update would have had with the group's updates applied in
+// lane order.  Each helper gathers the group (lanes at this call with the same
+// target word), lets its lowest lane perform the update, and releases the
+// group only after that RMW returned (__syncwarp), so no lane goes on before
+// its share of the update is done.
+
+__device__ __forceinline__ u32 group_of(const void* p) {
+    return __match_any_sync(__activemask(), reinterpret_cast<u64>(p));
+}
+
+// Threshold decrement by the group: returns this lane's old value (the value
+// minus the decrements of the lower lanes of its group).
+template <bool CNT = false>
+__device__ __forceinline__ i64 thr_dec_group(i64* thr) {
+    const u32 mask = group_of(thr);
+    const u32 leader = __ffs(mask) - 1;
+    u64 base = 0;
+    if (lane_id() == leader) {
+        oc_add<CNT>(kOcThr);
+        base = (u64)aref<i64>(*thr).fetch_add(-(i64)__popc(mask), kRlx);
+    }
+    base = __shfl_sync(mask, base, leader);
+    return (i64)base - (i64)__popc(mask & lanemask_lt());
+}
+
+// Threshold reset after installs: the group's lowest lane resets it (if it
+// changed) once for all of them; every lane's install precedes the reset.
+template <bool CNT = false>
+__device__ __forceinline__ void thr_reset_group(i64* thr, i64 v, unsigned int* err) {
+    const u32 mask = group_of(thr);
+    if (lane_id() == __ffs(mask) - 1 && ld_rlx(thr) != v) {
+        oc_add<CNT>(kOcThr);
+        thr_reset(thr, v, err);
+    }
+    __syncwarp(mask);
+}
+
+// Largest head of the group (tickets of concurrent operations lie within 2^31
+// of one another, so offsets from the lowest lane's head fit in 32 bits and
+// the maximum is taken modulo the counter width).
+__device__ __forceinline__ u64 group_max_head(u32 mask, u64 head) {
+    const u32 leader = __ffs(mask) - 1;
+    const u64 lead = __shfl_sync(mask, head, leader);
+    const int off = __reduce_max_sync(mask, (int)(i64)(head - lead));
+    return lead + (u64)(i64)off;
+}
+
+// Tail catch-up by the group: one atomic maximum to the largest head of the
+// group (returning, so it is performed before the group goes on).
+template <bool CNT = false>
+__device__ __forceinline__ void ring_catchup_group(const gq_ring_view& r, u64 head) {
+    const u32 mask = group_of(r.tail);
+    const u64 target = group_max_head(mask, head);
+    if (lane_id() == __ffs(mask) - 1) {
+        oc_add<CNT>(kOcCatch);
+        const u64 old = atomicMax(reinterpret_cast<unsigned long long*>(r.tail), target);
+        asm volatile("" ::"l"(old));
+    }
+    __syncwarp(mask);
+}
+
+// Due install (GPU-first): a dequeuer whose slot still holds an older cycle's
+// empty entry while Tail is past its ticket has a partner enqueuer that took
+// that ticket and will install there shortly.  Ruling the slot out at once
+// (Algorithm 1 TryDeq) sends both of them round for new tickets, and in
+// near-empty or near-full rings those retries feed each other (the partners of
+// the next tickets are overtaken in turn).  So the dequeuer first re-reads the
+// slot a bounded number of times, `due_wait` polls about 32 ns apart; after
+// that it proceeds exactly as TryDeq does with what it read last.  Waiting
+// changes no step of the protocol, only when the dequeuer takes it.  A Tail
+// moved by a catch-up (no partner) costs the wait and nothing else.  Off by
+// default (gq_options.due_wait): on the benchmark workloads it measured no
+// better than ruling the slot out at once; the batched form can tune it.
+template <bool CNT, class StillEmpty>
+__device__ __forceinline__ u64 wait_due_install(u64* slot, u64 e, u32 polls, StillEmpty still_empty) {
+    for (u32 w = 0; w < polls && still_empty(e); ++w) {
+        __nanosleep(32);
+        oc_add<CNT>(kOcSpin);
+        e = ld_acq(slot);
+    }
+    return e;
+}
+
 // Inner-ring enqueue of index `idx` (TryEnq of Algorithm 1, retried until it
 // succeeds).  Returns GQ_OK, or GQ_ERR_TIMEOUT if the retry bound expires.
 // tk (nullable, test recorder): receives the ticket the index was installed at.
-template <bool MATCH>
+template <bool MATCH, bool CNT = false>
 __device__ int lfq_ring_enq(const gq_dev& q, const gq_ring_view& r, u32 idx, u64* tk = nullptr) {
     for (u32 it = 0; it < kRetryLimit; ++it) {
-        const u64 t = warp_faa<MATCH>(r.tail, 1, q.batch_width);
+        const u64 t = warp_faa<MATCH, CNT>(r.tail, 1, q.batch_width);
         u64* slot = r.slots + (t & q.slot_mask);
         const u64 c = (t >> q.ring_order) & q.cycle_mask;
         const u64 ne = lfq_entry(c, kSafe, idx);
         u64 e = lfq_entry((c - 1) & q.cycle_mask, kSafe, kBotC);   // predicted current value
         bool done = cas(slot, e, ne);
+        oc_cas<CNT>(done);
         for (; !done && it < kRetryLimit; ++it) {
             if (!cyc_older(lfq_cycle(e), c, q) || lfq_index(e) < kBotC) break;
             if (!(e & kSafe)) {
@@ -99,13 +189,15 @@ __device__ int lfq_ring_enq(const gq_dev& q, const gq_ring_view& r, u32 idx, u64
                 if ((i64)(ld_rlx(r.head) - t) > 0) break;
             }
             done = cas(slot, e, ne);
+            oc_cas<CNT>(done);
             // CAS lost: e holds the current entry; re-evaluate the same ticket
         }
         if (done) {
-            if (ld_rlx(r.threshold) != q.thr_reset) thr_reset(r.threshold, q.thr_reset, q.err);
+            thr_reset_group<CNT>(r.threshold, q.thr_reset, q.err);
             if (tk) *tk = t;
             return GQ_OK;
         }
+        oc_add<CNT>(kOcBurn);
         if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
     latch_error(q.err, GQ_ERR_TIMEOUT);
@@ -115,14 +207,18 @@ __device__ int lfq_ring_enq(const gq_dev& q, const gq_ring_view& r, u32 idx, u64
 // Inner-ring dequeue (TryDeq of Algorithm 1, retried while it returns RETRY).
 // Returns GQ_OK with *idx, GQ_EMPTY, or GQ_ERR_TIMEOUT.  tk (nullable): the
 // ticket the index was taken at.
-template <bool MATCH>
+template <bool MATCH, bool CNT = false>
 __device__ int lfq_ring_deq(const gq_dev& q, const gq_ring_view& r, u32* idx, u64* tk = nullptr) {
     if (ld_rlx(r.threshold) < 0) return GQ_EMPTY;
     for (u32 it = 0; it < kRetryLimit; ++it) {
-        const u64 h = warp_faa<MATCH>(r.head, 1, q.batch_width);
+        const u64 h = warp_faa<MATCH, CNT>(r.head, 1, q.batch_width);
         u64* slot = r.slots + (h & q.slot_mask);
         const u64 c = (h >> q.ring_order) & q.cycle_mask;
         u64 e = ld_acq(slot);
+        oc_add<CNT>(kOcLoad);
+        auto empty_older = [&](u64 x) { return lfq_index(x) >= kBotC && cyc_older(lfq_cycle(x), c, q); };
+        if (q.due_wait && empty_older(e) && (i64)(ld_rlx(r.tail) - h) > 0)
+            e = wait_due_install<CNT>(slot, e, q.due_wait, empty_older);
         for (; it < kRetryLimit; ++it) {
             const u64 ec = lfq_cycle(e);
             if (ec == c) {
@@ -130,8 +226,12 @@ __device__ int lfq_ring_deq(const gq_dev& q, const gq_ring_view& r, u32* idx, u6
                     *idx = lfq_index(e);
                     if (tk) *tk = h;
                     // relaxed: the acquire load of e already ordered the payload read
-                    if (!aref<u64>(*slot).compare_exchange_strong(e, (e & ~0xFFFFFFFFull) | kBotC, kRlx, kRlx))
+                    const bool ok = aref<u64>(*slot).compare_exchange_strong(e, (e & ~0xFFFFFFFFull) | kBotC, kRlx, kRlx);
+                    oc_cas<CNT>(ok);
+                    if (!ok) {
+                        oc_add<CNT>(kOcRmw);
                         aref<u64>(*slot).fetch_or(kBotC, kRlx);
+                    }
                     return GQ_OK;
                 }
                 break;
@@ -141,15 +241,18 @@ __device__ int lfq_ring_deq(const gq_dev& q, const gq_ring_view& r, u32* idx, u6
             // occupied by an older cycle: clear Safe so the enqueuer of t = h
             // does not reuse it once Head has passed h.
             const u64 ne = (lfq_index(e) >= kBotC) ? lfq_entry(c, e & kSafe, kBot) : (e & ~kSafe);
-            if (cas(slot, e, ne)) break;
+            const bool ok = cas(slot, e, ne);
+            oc_cas<CNT>(ok);
+            if (ok) break;
         }
+        oc_add<CNT>(kOcBurn);
         const u64 tl = ld_rlx(r.tail);
         if ((i64)(tl - (h + 1)) <= 0) {
-            ring_catchup(r, h + 1);
-            thr_dec(r.threshold);
+            ring_catchup_group<CNT>(r, h + 1);
+            thr_dec_group<CNT>(r.threshold);
             return GQ_EMPTY;
         }
-        if (thr_dec(r.threshold) <= 0) return GQ_EMPTY;
+        if (thr_dec_group<CNT>(r.threshold) <= 0) return GQ_EMPTY;
         if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
     latch_error(q.err, GQ_ERR_TIMEOUT);
@@ -170,10 +273,10 @@ __device__ __forceinline__ T data_load(const gq_dev& q, u32 i) {
 
 // tk (nullable, test recorder): the aq ticket of the operation (an item's
 // enqueue and its dequeue share it).
-template <class T, bool MATCH>
+template <class T, bool MATCH, bool CNT = false>
 __device__ int lfq_enqueue(const gq_dev& q, T v, u64* tk = nullptr) {
     u32 i;
-    int s = lfq_ring_deq<MATCH>(q, q.fq, &i);
+    int s = lfq_ring_deq<MATCH, CNT>(q, q.fq, &i);
     if (s == GQ_EMPTY) return GQ_FULL;
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {                            // never expected: a corrupt ring entry
@@ -181,20 +284,20 @@ __device__ int lfq_enqueue(const gq_dev& q, T v, u64* tk = nullptr) {
         return GQ_ERR_INVALID;
     }
     data_store<T>(q, i, v);                           // ordered before the release CAS in aq
-    return lfq_ring_enq<MATCH>(q, q.aq, i, tk);
+    return lfq_ring_enq<MATCH, CNT>(q, q.aq, i, tk);
 }
 
-template <class T, bool MATCH>
+template <class T, bool MATCH, bool CNT = false>
 __device__ int lfq_dequeue(const gq_dev& q, T* v, u64* tk = nullptr) {
     u32 i;
-    int s = lfq_ring_deq<MATCH>(q, q.aq, &i, tk);
+    int s = lfq_ring_deq<MATCH, CNT>(q, q.aq, &i, tk);
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {                            // never expected: a corrupt ring entry
         latch_error(q.err, GQ_ERR_INVALID);
         return GQ_ERR_INVALID;
     }
     *v = data_load<T>(q, i);                          // after the acquire on the aq slot
-    s = lfq_ring_enq<MATCH>(q, q.fq, i);              // release: the read precedes reuse
+    s = lfq_ring_enq<MATCH, CNT>(q, q.fq, i);         // release: the read precedes reuse
     return s == GQ_OK ? GQ_OK : s;
 }
 
@@ -205,12 +308,12 @@ __device__ int lfq_dequeue(const gq_dev& q, T* v, u64* tk = nullptr) {
 // mix enqueues and dequeues run them together instead of one after the other
 // (divergent branches); WaveFAA groups the lanes by counter address.  Each
 // lane performs exactly the steps of its own operation.
-template <class T>
+template <class T, bool CNT = false>
 __device__ int lfq_op(const gq_dev& q, bool enq, T* v, u64* tk = nullptr) {
     const gq_ring_view& from = enq ? q.fq : q.aq;
     const gq_ring_view& to = enq ? q.aq : q.fq;
     u32 i;
-    int s = lfq_ring_deq<true>(q, from, &i, enq ? nullptr : tk);
+    int s = lfq_ring_deq<true, CNT>(q, from, &i, enq ? nullptr : tk);
     if (s == GQ_EMPTY) return enq ? GQ_FULL : GQ_EMPTY;
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {                            // never expected: a corrupt ring entry
@@ -219,7 +322,7 @@ __device__ int lfq_op(const gq_dev& q, bool enq, T* v, u64* tk = nullptr) {
     }
     if (enq) data_store<T>(q, i, *v);                 // ordered before the release CAS in aq
     else *v = data_load<T>(q, i);                     // after the acquire on the aq slot
-    return lfq_ring_enq<true>(q, to, i, enq ? tk : nullptr);
+    return lfq_ring_enq<true, CNT>(q, to, i, enq ? tk : nullptr);
 }
 
 }  // namespace gqd

@@ -14,28 +14,29 @@ namespace gqd {
 // tk (nullable, test recorder only): receives the operation's ticket in the
 // allocated-index ring (G-LFQ, G-WFQ) or its cell (G-WFQ-YMC); an item's
 // enqueue and the dequeue that returns it get the same one.
-template <class T, int KIND, bool MATCH = false>
+// CNT: the counting instantiation (per-thread event counts, see gq_atomics.cuh).
+template <class T, int KIND, bool MATCH = false, bool CNT = false>
 __device__ __forceinline__ int queue_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
-    if constexpr (KIND == GQ_LFQ) return lfq_enqueue<T, MATCH>(q, v, tk);
-    else if constexpr (KIND == GQ_WFQ) return wfq_enqueue<T, MATCH>(q, v, tid, tk);
-    else return ymc_enqueue<T, MATCH>(q, v, tid, tk);
+    if constexpr (KIND == GQ_LFQ) return lfq_enqueue<T, MATCH, CNT>(q, v, tk);
+    else if constexpr (KIND == GQ_WFQ) return wfq_enqueue<T, MATCH, CNT>(q, v, tid, tk);
+    else return ymc_enqueue<T, MATCH, CNT>(q, v, tid, tk);
 }
 
-template <class T, int KIND, bool MATCH = false>
+template <class T, int KIND, bool MATCH = false, bool CNT = false>
 __device__ __forceinline__ int queue_dequeue(const gq_dev& q, T* v, u32 tid, u64* tk = nullptr) {
-    if constexpr (KIND == GQ_LFQ) return lfq_dequeue<T, MATCH>(q, v, tk);
-    else if constexpr (KIND == GQ_WFQ) return wfq_dequeue<T, MATCH>(q, v, tid, tk);
-    else return ymc_dequeue<T, MATCH>(q, v, tid, tk);
+    if constexpr (KIND == GQ_LFQ) return lfq_dequeue<T, MATCH, CNT>(q, v, tk);
+    else if constexpr (KIND == GQ_WFQ) return wfq_dequeue<T, MATCH, CNT>(q, v, tid, tk);
+    else return ymc_dequeue<T, MATCH, CNT>(q, v, tid, tk);
 }
 
 // Enqueue (enq, payload *v) or dequeue (!enq, result in *v) chosen per lane.
 // G-LFQ and G-WFQ run both on one code path (their operations mirror each
 // other over the two index rings); G-WFQ-YMC branches.
-template <class T, int KIND>
+template <class T, int KIND, bool CNT = false>
 __device__ __forceinline__ int queue_op(const gq_dev& q, bool enq, T* v, u32 tid, u64* tk = nullptr) {
-    if constexpr (KIND == GQ_LFQ) return lfq_op<T>(q, enq, v, tk);
-    else if constexpr (KIND == GQ_WFQ) return wfq_op<T>(q, enq, v, tid, tk);
-    else return enq ? ymc_enqueue<T, false>(q, *v, tid, tk) : ymc_dequeue<T, false>(q, v, tid, tk);
+    if constexpr (KIND == GQ_LFQ) return lfq_op<T, CNT>(q, enq, v, tk);
+    else if constexpr (KIND == GQ_WFQ) return wfq_op<T, CNT>(q, enq, v, tid, tk);
+    else return enq ? ymc_enqueue<T, false, CNT>(q, *v, tid, tk) : ymc_dequeue<T, false, CNT>(q, v, tid, tk);
 }
 
 }  // namespace gqd

@@ -213,6 +213,22 @@ __device__ __forceinline__ void wfq_catchup(const gq_ring_view& R, u64 head) {
     }
 }
 
+// Catch-up by the converged lanes that catch up the same Tail word: the
+// group's lowest lane raises it to the group's largest target (modulo 2^43),
+// once, and the group goes on after that (see the group helpers of G-LFQ).
+template <bool CNT = false>
+__device__ __forceinline__ void wfq_catchup_group(const gq_ring_view& R, u64 head) {
+    const u32 mask = group_of(R.tail);
+    const u32 leader = __ffs(mask) - 1;
+    const u64 lead = __shfl_sync(mask, head, leader);
+    const int off = __reduce_max_sync(mask, (int)((i64)(((head - lead) & kCntMask) << 21) >> 21));
+    if (lane_id() == leader) {
+        oc_add<CNT>(kOcCatch);
+        wfq_catchup(R, (lead + (u64)(i64)off) & kCntMask);
+    }
+    __syncwarp(mask);
+}
+
 // Finishes the slow enqueue that installed entry e (Enq = 0) at ticket t:
 // FIN on its request at t (owner looked up by index), then Enq = 1.
 static __device__ __noinline__ void wfq_finalize(const gq_ring_view& R, u64* slot, u64 e, u64 t, const gq_dev& q) {
@@ -236,9 +252,9 @@ static __device__ __noinline__ void wfq_finalize(const gq_ring_view& R, u64* slo
 // ---- fast path (Algorithm 1 on the G-WFQ entry) ----------------------------
 enum { kTryOk = 0, kTryEmpty = 2, kTryRetry = 3 };
 
-template <bool MATCH>
+template <bool MATCH, bool CNT = false>
 __device__ int wfq_try_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u64* t_out) {
-    const u64 t = warp_faa<MATCH>(R.tail, kGOne, q.batch_width) >> kGThrBits & kCntMask;
+    const u64 t = warp_faa<MATCH, CNT>(R.tail, kGOne, q.batch_width) >> kGThrBits & kCntMask;
     *t_out = t;
     u64* slot = R.slots + (t & q.slot_mask);
     const u64 c = (t >> q.ring_order) & q.cycle_mask;
@@ -246,42 +262,57 @@ __device__ int wfq_try_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u64*
     const u64 cm1 = (c - 1) & q.cycle_mask;
     u64 e = wfq_entry((c - 2) & q.cycle_mask, cm1, 1, 1, kWBotC);
     bool done = cas(slot, e, wfq_entry(cm1, c, 1, 1, idx));
+    oc_cas<CNT>(done);
     for (u32 it = 0; !done && it < kRetryLimit; ++it) {
         if (!cyc_older(w_cyc(e), c, q) || w_idx(e) < kWBotC) break;
         if (!(e & kWSafe) && !cnt_le(g_cnt(ld_rlx(R.head)), t)) break;
         done = cas(slot, e, wfq_entry(note_fresh(w_note(e), c, q), c, 1, 1, idx));
+        oc_cas<CNT>(done);
     }
-    if (!done) return kTryRetry;
-    if (ld_rlx(R.threshold) != q.thr_reset) thr_reset(R.threshold, q.thr_reset, q.err);
+    if (!done) {
+        oc_add<CNT>(kOcBurn);
+        return kTryRetry;
+    }
+    thr_reset_group<CNT>(R.threshold, q.thr_reset, q.err);
     return kTryOk;
 }
 
 // Consumes the item of ticket h in `slot` (its cycle already checked).
 // Consume: index field to BOTC, other fields kept (CAS from the entry read,
 // OR as the fallback); e was read with acquire, so the consume can be relaxed.
+template <bool CNT = false>
 __device__ __forceinline__ u32 wfq_consume(const gq_ring_view& R, u64* slot, u64 e, u64 h, const gq_dev& q) {
     if (!(e & kWEnq)) {
         wfq_finalize(R, slot, e, h, q);
         e |= kWEnq;
     }
     const u32 i = w_idx(e);
-    if (!aref<u64>(*slot).compare_exchange_strong(e, (e & ~(u64)kWIdxMask) | kWBotC, kRlx, kRlx))
+    const bool ok = aref<u64>(*slot).compare_exchange_strong(e, (e & ~(u64)kWIdxMask) | kWBotC, kRlx, kRlx);
+    oc_cas<CNT>(ok);
+    if (!ok) {
+        oc_add<CNT>(kOcRmw);
         aref<u64>(*slot).fetch_or(kWBotC, kRlx);
+    }
     return i;
 }
 
-template <bool MATCH>
+template <bool MATCH, bool CNT = false>
 __device__ int wfq_try_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u64* h_out) {
-    const u64 h = warp_faa<MATCH>(R.head, kGOne, q.batch_width) >> kGThrBits & kCntMask;
+    const u64 h = warp_faa<MATCH, CNT>(R.head, kGOne, q.batch_width) >> kGThrBits & kCntMask;
     *h_out = h;
     u64* slot = R.slots + (h & q.slot_mask);
     const u64 c = (h >> q.ring_order) & q.cycle_mask;
     u64 e = ld_acq(slot);
+    oc_add<CNT>(kOcLoad);
+    // due install (see wait_due_install): Tail's Counter past h
+    auto empty_older = [&](u64 x) { return w_idx(x) >= kWBotC && cyc_older(w_cyc(x), c, q); };
+    if (q.due_wait && empty_older(e) && cnt_lt(h, g_cnt(ld_rlx(R.tail))))
+        e = wait_due_install<CNT>(slot, e, q.due_wait, empty_older);
     for (u32 it = 0; it < kRetryLimit; ++it) {
         const u64 ec = w_cyc(e);
         if (ec == c) {
             if (w_idx(e) < kWBotC) {
-                *idx = wfq_consume(R, slot, e, h, q);
+                *idx = wfq_consume<CNT>(R, slot, e, h, q);
                 return kTryOk;
             }
             break;
@@ -290,19 +321,22 @@ __device__ int wfq_try_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u64
         const u64 ne = (w_idx(e) >= kWBotC)
                            ? wfq_entry(note_fresh(w_note(e), c, q), c, e & kWSafe, 1, kWBot)
                            : (e & ~kWSafe);
-        if (cas(slot, e, ne)) break;
+        const bool ok = cas(slot, e, ne);
+        oc_cas<CNT>(ok);
+        if (ok) break;
         if (it + 1 == kRetryLimit) {
             latch_error(q.err, GQ_ERR_TIMEOUT);
             return kTryRetry;
         }
     }
+    oc_add<CNT>(kOcBurn);
     const u64 tl = g_cnt(ld_rlx(R.tail));
     if (cnt_le(tl, h + 1)) {
-        wfq_catchup(R, h + 1);
-        thr_dec(R.threshold);
+        wfq_catchup_group<CNT>(R, h + 1);
+        thr_dec_group<CNT>(R.threshold);
         return kTryEmpty;
     }
-    if (thr_dec(R.threshold) <= 0) return kTryEmpty;
+    if (thr_dec_group<CNT>(R.threshold) <= 0) return kTryEmpty;
     return kTryRetry;
 }
 
@@ -463,19 +497,20 @@ static __device__ __noinline__ u64 wfq_slow_request(const gq_ring_view& R, const
 
 // Inner-ring enqueue of index idx by thread `me`.  tk (nullable, test
 // recorder): the ticket the index was installed at, fast or slow.
-template <bool MATCH>
+template <bool MATCH, bool CNT = false>
 __device__ int wfq_ring_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u32 me, u32 patience,
                             u64* tk = nullptr) {
     wfq_maybe_help(R, q, me);
     u64 t = 0;
     for (u32 p = 0; p < patience; ++p) {
-        if (wfq_try_enq<MATCH>(R, q, idx, &t) == kTryOk) {
+        if (wfq_try_enq<MATCH, CNT>(R, q, idx, &t) == kTryOk) {
             if (tk) *tk = t;
             return GQ_OK;
         }
         if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
     if (patience == 0) t = (g_cnt(ld_rlx(R.tail)) - 1) & kCntMask;   // a ticket value r never held
+    oc_add<CNT>(kOcSlow);
     const u64 l = wfq_slow_request(R, q, me, true, t, idx);
     if (!l) {
         latch_error(q.err, GQ_ERR_TIMEOUT);
@@ -496,14 +531,14 @@ __device__ int wfq_ring_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u32
 
 // Inner-ring dequeue by thread `me`: GQ_OK with *idx, or GQ_EMPTY.  tk
 // (nullable): the ticket the index was taken at.
-template <bool MATCH>
+template <bool MATCH, bool CNT = false>
 __device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u32 me, u32 patience,
                             u64* tk = nullptr) {
     if (ld_rlx(R.threshold) < 0) return GQ_EMPTY;
     wfq_maybe_help(R, q, me);
     u64 h = 0;
     for (u32 p = 0; p < patience; ++p) {
-        const int s = wfq_try_deq<MATCH>(R, q, idx, &h);
+        const int s = wfq_try_deq<MATCH, CNT>(R, q, idx, &h);
         if (s == kTryOk) {
             if (tk) *tk = h;
             return GQ_OK;
@@ -512,6 +547,7 @@ __device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u3
         if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
     if (patience == 0) h = (g_cnt(ld_rlx(R.head)) - 1) & kCntMask;
+    oc_add<CNT>(kOcSlow);
     const u64 l = wfq_slow_request(R, q, me, false, h, 0);
     if (!l) {
         latch_error(q.err, GQ_ERR_TIMEOUT);
@@ -531,14 +567,14 @@ __device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u3
 }
 
 // tk (nullable, test recorder): the aq ticket of the operation.
-template <class T, bool MATCH>
+template <class T, bool MATCH, bool CNT = false>
 __device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
     }
     u32 i;
-    int s = wfq_ring_deq<MATCH>(q.fq, q, &i, tid, q.patience_deq);
+    int s = wfq_ring_deq<MATCH, CNT>(q.fq, q, &i, tid, q.patience_deq);
     if (s == GQ_EMPTY) return GQ_FULL;
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {
@@ -546,30 +582,30 @@ __device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
         return GQ_ERR_INVALID;
     }
     data_store<T>(q, i, v);
-    return wfq_ring_enq<MATCH>(q.aq, q, i, tid, q.patience_enq, tk);
+    return wfq_ring_enq<MATCH, CNT>(q.aq, q, i, tid, q.patience_enq, tk);
 }
 
-template <class T, bool MATCH>
+template <class T, bool MATCH, bool CNT = false>
 __device__ int wfq_dequeue(const gq_dev& q, T* v, u32 tid, u64* tk = nullptr) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
     }
     u32 i;
-    int s = wfq_ring_deq<MATCH>(q.aq, q, &i, tid, q.patience_deq, tk);
+    int s = wfq_ring_deq<MATCH, CNT>(q.aq, q, &i, tid, q.patience_deq, tk);
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {
         latch_error(q.err, GQ_ERR_INVALID);
         return GQ_ERR_INVALID;
     }
     *v = data_load<T>(q, i);
-    s = wfq_ring_enq<MATCH>(q.fq, q, i, tid, q.patience_enq);
+    s = wfq_ring_enq<MATCH, CNT>(q.fq, q, i, tid, q.patience_enq);
     return s == GQ_OK ? GQ_OK : s;
 }
 
 // Enqueue or dequeue on one code path (see lfq_op): the rings are chosen per
 // lane, so mixed warps run both kinds of operation together.
-template <class T>
+template <class T, bool CNT = false>
 __device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid, u64* tk = nullptr) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
@@ -578,7 +614,7 @@ __device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid, u64* tk = nullpt
     const gq_ring_view& from = enq ? q.fq : q.aq;
     const gq_ring_view& to = enq ? q.aq : q.fq;
     u32 i;
-    int s = wfq_ring_deq<true>(from, q, &i, tid, q.patience_deq, enq ? nullptr : tk);
+    int s = wfq_ring_deq<true, CNT>(from, q, &i, tid, q.patience_deq, enq ? nullptr : tk);
     if (s == GQ_EMPTY) return enq ? GQ_FULL : GQ_EMPTY;
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {
@@ -587,7 +623,7 @@ __device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid, u64* tk = nullpt
     }
     if (enq) data_store<T>(q, i, *v);
     else *v = data_load<T>(q, i);
-    return wfq_ring_enq<true>(to, q, i, tid, q.patience_enq, enq ? tk : nullptr);
+    return wfq_ring_enq<true, CNT>(to, q, i, tid, q.patience_enq, enq ? tk : nullptr);
 }
 
 }  // namespace gqd

@@ -98,11 +98,16 @@ enum { kYValue = 0, kYUnusable = 1, kYEmpty = 2 };
 
 // help_enq: settles cell i for the dequeuer `me` and returns kYValue with *v,
 // kYUnusable (try another cell), or kYEmpty (T <= i: no enqueue reached i).
+template <bool CNT = false>
 static __device__ __noinline__ int ymc_help_enq(const gq_dev& q, u32 me, u64 i, u64* v) {
     u64* cv = q.cell_val + i;
     u64* ce = q.cell_enq + i;
     u64 x = ld_acq(cv);
-    for (u32 s = 0; s < kYSpin && x == kVBot; ++s) x = ld_acq(cv);   // an enqueuer may be on its way
+    oc_add<CNT>(kOcLoad);
+    for (u32 s = 0; s < kYSpin && x == kVBot; ++s) {   // an enqueuer may be on its way
+        oc_add<CNT>(kOcSpin);
+        x = ld_acq(cv);
+    }
     if (x == kVBot && ld_acq(q.ymc_tail) > i) {
         // T > i: the enqueuer holding ticket i has taken it and its write is
         // due.  Marking the cell unusable now would send that enqueuer round
@@ -110,12 +115,16 @@ static __device__ __noinline__ int ymc_help_enq(const gq_dev& q, u32 me, u64 i, 
         // of T, more cells are found empty, more enqueuers retry).  Wait
         // longer for the write, boundedly.
         for (u32 s = 0; s < kYWaitPolls && x == kVBot; ++s) {
+            oc_add<CNT>(kOcSpin);
             __nanosleep(64);
             x = ld_acq(cv);
         }
     }
     if (x == kVBot) {
-        if (!cas(cv, x, kVTop) && x != kVTop) { *v = x; return kYValue; }
+        const bool ok = cas(cv, x, kVTop);
+        oc_cas<CNT>(ok);
+        if (ok) oc_add<CNT>(kOcMark);
+        if (!ok && x != kVTop) { *v = x; return kYValue; }
         x = kVTop;
     } else if (x != kVTop) {
         *v = x;
@@ -248,7 +257,7 @@ static __device__ __noinline__ void ymc_help_deq(const gq_dev& q, u32 me, u32 p)
 
 // tk (nullable, test recorder): the cell of the operation (an item's enqueue
 // and its dequeue share it).
-template <class T, bool MATCH>
+template <class T, bool MATCH, bool CNT = false>
 __device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
@@ -258,20 +267,24 @@ __device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
     if (x >= kVTop) return GQ_ERR_RESERVED_VALUE;
     u64 id = 0;
     for (u32 p = 0; p <= q.patience_enq; ++p) {
-        const u64 i = warp_faa<MATCH>(q.ymc_tail, 1, q.batch_width);
+        const u64 i = warp_faa<MATCH, CNT>(q.ymc_tail, 1, q.batch_width);
         if (!ycell_ok(q, i)) return GQ_ERR_POOL_EXHAUSTED;
         u64 b = kVBot;
-        if (aref<u64>(q.cell_val[i]).compare_exchange_strong(b, x, kRel, kRlx)) {
+        const bool ok = aref<u64>(q.cell_val[i]).compare_exchange_strong(b, x, kRel, kRlx);
+        oc_cas<CNT>(ok);
+        if (ok) {
             if (tk) *tk = i;
             return GQ_OK;
         }
+        oc_add<CNT>(kOcBurn);
         id = i;
         if (q.backoff_ns) __nanosleep(q.backoff_ns);
     }
+    oc_add<CNT>(kOcSlow);
     return ymc_enq_slow(q, tid, x, id, tk);
 }
 
-template <class T, bool MATCH>
+template <class T, bool MATCH, bool CNT = false>
 __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid, u64* tk = nullptr) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
@@ -283,17 +296,21 @@ __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid, u64* tk = nullptr) 
     u64 id = 0, v = 0;
     int res = kYUnusable;
     for (u32 p = 0; p <= q.patience_deq && res == kYUnusable; ++p) {
-        const u64 i = warp_faa<MATCH>(q.ymc_head, 1, q.batch_width);
+        const u64 i = warp_faa<MATCH, CNT>(q.ymc_head, 1, q.batch_width);
         if (!ycell_ok(q, i)) return GQ_ERR_POOL_EXHAUSTED;
-        res = ymc_help_enq(q, tid, i, &v);
+        res = ymc_help_enq<CNT>(q, tid, i, &v);
         if (res == kYValue) {
             u64 b = kRefBot;
-            if (!cas(q.cell_deq + i, b, kRefTop)) res = kYUnusable;   // a slow dequeue took it
+            const bool ok = cas(q.cell_deq + i, b, kRefTop);
+            oc_cas<CNT>(ok);
+            if (!ok) res = kYUnusable;   // a slow dequeue took it
         }
+        if (res != kYValue) oc_add<CNT>(kOcBurn);
         id = i;
         if (res == kYUnusable && q.backoff_ns) __nanosleep(q.backoff_ns);
     }
     if (res == kYUnusable) {
+        oc_add<CNT>(kOcSlow);
         // slow path: publish <id, idx = id> and help it to completion
         u64* dr = yrec(q, tid);
         st_rel(dr + kYDrId, id);

@@ -162,6 +162,22 @@ def test_split_producer_consumer(kind, frac):
         assert rep["deq_empty"] > 0
 
 
+@pytest.mark.parametrize("kind", ["lfq", "wfq"])
+@pytest.mark.parametrize("frac", [0.1, 0.9])
+def test_split_with_due_install_wait(kind, frac):
+    """The ring queues with the due-install wait on (a dequeuer re-reads a slot
+    whose enqueuer is due before ruling it out): same checks as the plain run."""
+    T, total, cap = 1 << 16, 1 << 21, 1 << 12
+    P = int(frac * T)
+    q = make_queue(kind, cap, 8, max_threads=T, due_wait=64)
+    r = run_log(q, gq.GQ_RUN_SPLIT, T, producers=P, total_ops=total, tickets=True)
+    left = drain(q, total)
+    rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
+    assert rep["violations"] == 0, str(rep)
+    tr = oracle.check_tickets(r["kind"], r["status"], r["val"], r["ticket"], bits=43 if kind == "wfq" else 64)
+    assert tr["violations"] == 0, str(tr)
+
+
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("T", [1 << 10, 1 << 14, 1 << 20])
 def test_enqueue_then_dequeue_phases(kind, T):
