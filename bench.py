@@ -221,7 +221,9 @@ def bench_apps(gq, synth, kinds, dev, reps=3):
     return out
 
 
-def _timed(fn, reps):
+def _timed(fn, reps, spread=None):
+    """Median device time (ms) of `reps` timed calls after an untimed one;
+    `spread` (a list) receives (min, max)."""
     import torch
     fn()
     torch.cuda.synchronize()
@@ -233,6 +235,8 @@ def _timed(fn, reps):
         e1.record()
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
+    if spread is not None:
+        spread[:] = [min(ms), max(ms)]
     return float(np.median(ms))
 
 
@@ -273,15 +277,21 @@ def bench_batched(gq, synth, kinds, dev, reps=7):
             mq.run(TPQ, PPQ, OPQ, counts)
 
         res = {}
-        t = _timed(per_call, reps)
-        res["per_call_mops"] = round(succ() / (t * 1e-3) / 1e6, 1)
-        t = _timed(persistent, reps)
-        res["persistent_mops"] = round(succ() / (t * 1e-3) / 1e6, 1)
+
+        def mops(name, fn):
+            sp = []
+            t = _timed(fn, reps, sp)
+            ok = succ()
+            res[name + "_mops"] = round(ok / (t * 1e-3) / 1e6, 1)
+            # Mops/s of the slowest and the fastest repetition (the last one's operation count)
+            res[name + "_mops_range"] = [round(ok / (sp[1] * 1e-3) / 1e6, 1), round(ok / (sp[0] * 1e-3) / 1e6, 1)]
+
+        mops("per_call", per_call)
+        mops("persistent", persistent)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             persistent()
-        t = _timed(g.replay, reps)
-        res["graph_mops"] = round(succ() / (t * 1e-3) / 1e6, 1)
+        mops("graph", g.replay)
         best = autotune.tune_multi(mq, TPQ, PPQ, OPQ, widths=(32, 16, 8), blocks_per_sm=(0, 4), backoffs=(0, 200),
                                    reps=3)
         g2 = torch.cuda.CUDAGraph()
@@ -289,8 +299,7 @@ def bench_batched(gq, synth, kinds, dev, reps=7):
             counts.zero_()
             mq.reset()
             mq.run(TPQ, PPQ, OPQ, counts, blocks=best["blocks"])
-        t = _timed(g2.replay, reps)
-        res["tuned_graph_mops"] = round(succ() / (t * 1e-3) / 1e6, 1)
+        mops("tuned_graph", g2.replay)
         res["tuned"] = {kk: best[kk] for kk in ("batch_width", "blocks", "backoff_ns", "patience", "help_delay")}
         out["queues256_%s" % k] = res
         mq.close()
@@ -321,7 +330,7 @@ def bench_batched(gq, synth, kinds, dev, reps=7):
     return out
 
 
-def bench_serving(gq, synth, kinds, dev, pool_graphs=64, seed=2026):
+def bench_serving(gq, synth, kinds, dev, pool_graphs=1000, seed=2026):
     """BFS serving: a resident pool of R-MAT graphs (scale uniform in 10..20 by
     seed, i.e. log-uniform vertex counts), requests (graph, source) with Poisson
     arrivals at 100..10,000 req/s, admission against a 32 GiB budget.  Persistent
@@ -330,11 +339,14 @@ def bench_serving(gq, synth, kinds, dev, pool_graphs=64, seed=2026):
     Latency = host-observed completion - arrival."""
     import torch
     scales = synth.rmat_pool_scales(pool_graphs, 10, 20, seed)
-    host = [synth.rmat_csr_fast(int(sc), seed=seed * 1000 + i) for i, sc in enumerate(scales)]
-    devg = [(torch.from_numpy(o.view(np.int64)).to(dev), torch.from_numpy(a.view(np.int32)).to(dev)) for o, a in host]
-    offs = [h[0] for h in host]
-    out = {"pool": {"graphs": pool_graphs, "scales": "uniform 10..20", "edges": int(sum(len(a) for _, a in host)),
-                    "budget_gib": 32}}
+    t0 = time.perf_counter()
+    # the pool is generated on the device (same graphs as the host generator)
+    devg = [synth.rmat_csr_torch(int(sc), seed=seed * 1000 + i, device=dev) for i, sc in enumerate(scales)]
+    offs = [o.cpu().numpy().view(np.uint64) for o, _ in devg]
+    gen_s = time.perf_counter() - t0
+    out = {"pool": {"graphs": pool_graphs, "scales": "uniform 10..20", "edges": int(sum(a.numel() for _, a in devg)),
+                    "device_gib": round(sum(o.numel() * 8 + a.numel() * 4 for o, a in devg) / 2**30, 2),
+                    "generated_s": round(gen_s, 1), "budget_gib": 32}}
     for rate in (100, 300, 1000, 3000, 10000):
         nreq = int(min(2000, max(200, rate)))
         gid, src, arr = synth.serving_requests(offs, nreq, float(rate), seed + rate)

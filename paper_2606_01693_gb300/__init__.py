@@ -152,11 +152,18 @@ def _need(t, n: int, elem: int, what: str) -> None:
         raise GqError(GQ_ERR_INVALID, what + " (holds %d bytes, needs %d)" % (t.numel() * t.element_size(), n * elem))
 
 
+_ELEM_BYTES: dict = {}   # payload width of the handles made through this module
+
+
 def _elem_bytes(h: int) -> int:
-    """Payload width of a queue handle, read from its device view."""
-    buf = (ctypes.c_uint8 * GQ_VIEW_BYTES)()
-    _check(load().gq_device_view(h, buf), "gq_device_view")
-    return int.from_bytes(bytes(buf[4:8]), "little")
+    """Payload width of a queue handle (remembered from gq_create, else read
+    from its device view)."""
+    eb = _ELEM_BYTES.get(h)
+    if eb is None:
+        buf = (ctypes.c_uint8 * GQ_VIEW_BYTES)()
+        _check(load().gq_device_view(h, buf), "gq_device_view")
+        eb = int.from_bytes(bytes(buf[4:8]), "little")
+    return eb
 
 
 def _stream(stream=None) -> int | None:
@@ -182,10 +189,12 @@ def gq_create(kind: int, capacity: int, elem_bytes: int, max_threads: int, opt: 
     h = ctypes.c_void_p(0)
     _check(load().gq_create(kind, capacity, elem_bytes, max_threads, ctypes.byref(opt) if opt else None,
                             _ptr(workspace), _stream(stream), ctypes.byref(h)), "gq_create")
+    _ELEM_BYTES[h.value] = elem_bytes
     return h.value
 
 
 def gq_destroy(h: int) -> None:
+    _ELEM_BYTES.pop(h, None)
     _check(load().gq_destroy(h), "gq_destroy")
 
 

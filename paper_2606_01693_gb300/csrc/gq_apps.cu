@@ -130,6 +130,16 @@ __global__ void __launch_bounds__(256) k_bfs(const __grid_constant__ gq_dev qa, 
 }
 
 template <int KIND>
+int bfs_grid_threads(uint64_t* threads) {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs<KIND>, 256, 0) != cudaSuccess || occ < 1)
+        return GQ_ERR_CUDA;
+    *threads = (uint64_t)occ * (uint64_t)sms * 256;
+    return GQ_OK;
+}
+
+template <int KIND>
 int launch_bfs(gq_handle ha, gq_handle hb, uint64_t n, const uint64_t* off, const uint32_t* adj, uint32_t src,
                uint32_t* dist, unsigned long long* stats, cudaStream_t st) {
     int occ = 0;
@@ -291,6 +301,15 @@ extern "C" int gq_bfs_batch(gq_handle id_queue, const gq_handle* frontier, uint3
         case GQ_LFQ: return launch_bfs_batch<GQ_LFQ>(id_queue, frontier, slots, cluster_blocks, d_instances, d_order, ninst, d_workspace, d_stats, st);
         case GQ_WFQ: return launch_bfs_batch<GQ_WFQ>(id_queue, frontier, slots, cluster_blocks, d_instances, d_order, ninst, d_workspace, d_stats, st);
         default: return launch_bfs_batch<GQ_YMC>(id_queue, frontier, slots, cluster_blocks, d_instances, d_order, ninst, d_workspace, d_stats, st);
+    }
+}
+
+int gq_bfs_grid_threads(int kind, uint64_t* threads) {
+    switch (kind) {
+        case GQ_LFQ: return bfs_grid_threads<GQ_LFQ>(threads);
+        case GQ_WFQ: return bfs_grid_threads<GQ_WFQ>(threads);
+        case GQ_YMC: return bfs_grid_threads<GQ_YMC>(threads);
+        default: return GQ_ERR_INVALID;
     }
 }
 

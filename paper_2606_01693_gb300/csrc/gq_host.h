@@ -59,6 +59,11 @@ int gq_check_launch();
 // being captured into a CUDA graph then makes none).
 int gq_run_kernels_init(int device, int smem_optin);
 
+// Threads of one gq_bfs launch of this queue kind on the current device (its
+// cooperative grid: every resident 256-thread block); a G-WFQ / G-WFQ-YMC pair
+// of frontier queues needs that many per-thread records.
+int gq_bfs_grid_threads(int kind, uint64_t* threads);
+
 // Launch configuration for a grid-stride kernel whose threads need one record
 // each (G-WFQ, G-WFQ-YMC): never more threads than records.
 void gq_grid_for(const gq_queue* q, uint64_t n_items, int occupancy_blocks_per_sm, uint32_t block,

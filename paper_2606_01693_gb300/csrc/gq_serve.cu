@@ -500,8 +500,11 @@ struct PerRequest {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
     int init(u64 nmax, cudaStream_t st) {
-        // gq_bfs runs one thread per resident slot of the GPU (at most max_threads)
-        int s = fr.create(2, c.kind, queue_capacity(c.kind, nmax), 1u << 19, st);
+        // gq_bfs runs one thread per resident slot of the GPU: one record each
+        uint64_t bt = 0;
+        int s = gq_bfs_grid_threads(c.kind, &bt);
+        if (s != GQ_OK) return s;
+        s = fr.create(2, c.kind, queue_capacity(c.kind, nmax), (uint32_t)(bt < (1u << 20) ? bt : (1u << 20)), st);
         if (s != GQ_OK) return s;
         const u64 nev = c.nrequests < 1024 ? c.nrequests : 1024;
         ev.assign(nev, nullptr);
@@ -684,8 +687,16 @@ extern "C" int gq_serve(const gq_serve_config* cfg, gq_serve_result* res) {
     // per-graph state: CSR bytes need m = offsets[n], read once from the device
     std::vector<u64> graph_charge(c.ngraphs), graph_dist(c.ngraphs);
     u64 nmax = 1;
-    // queue records counted as the per-request form needs them (the larger), except in pure persistent mode
-    const u32 mt = c.mode == GQ_SERVE_PERSISTENT ? c.cluster_blocks * 256 : (1u << 19);
+    // Per-thread queue records (G-WFQ, G-WFQ-YMC) are counted for the threads
+    // that run a request: a cluster in the persistent scheduler, the whole
+    // cooperative grid of one gq_bfs launch otherwise (adaptive mode may run a
+    // request either way and counts the larger).
+    u32 mt = c.cluster_blocks * 256;
+    if (c.mode != GQ_SERVE_PERSISTENT) {
+        uint64_t bt = 0;
+        if ((s = gq_bfs_grid_threads(c.kind, &bt)) != GQ_OK) return res->status = s;
+        mt = (u32)(bt < (1u << 20) ? bt : (1u << 20));
+    }
     for (u32 g = 0; g < c.ngraphs; ++g) {
         const gq_bfs_instance& x = c.graphs[g];
         u64 m = 0;

@@ -147,13 +147,24 @@ __device__ __forceinline__ bool req_live(const gq_ring_view& R, u32 r, u64 seq) 
 // sequence `seq`) on `side` (0 tail, 1 head).  *v: the last ticket this helper
 // tried for r; on true it holds the new ticket.  Returns false when the request
 // is finished (FIN) or no longer live.
+// A helper whose CAS on the Global word lost sleeps before its next try, from
+// kSlowNapMin ns doubling up to kSlowNapMax: with thousands of requests on
+// the slow path at once (a ring far smaller than the number of threads) the
+// helpers otherwise hammer one word that only one of them can win per round.
+// Lost CASes are counted locally and added to the statistics line once per
+// call, not once each (that line is one more hot word).
+constexpr u32 kSlowNapMin = 64, kSlowNapMax = 8192;
+
 static __device__ __noinline__ bool slow_faa(const gq_ring_view& R, int side, u32 r, u64 seq, u32 me, u64* v, i64* thld,
                          const gq_dev& q, u32* budget) {
     u64* G = side ? R.head : R.tail;
     u64* L = rec_of(R, r) + (side ? kRLocalHead : kRLocalTail);
     u64* P2 = rec_of(R, me) + (side ? kRP2Head : kRP2Tail);
     u64 last = ~0ull;
-    u32 stall = 0;
+    u32 stall = 0, lost = 0, nap = 0;
+    auto flush = [&]() {
+        if (lost && q.scratch) atomicAdd(q.scratch + kStatGlobalCasFail, (unsigned long long)lost);
+    };
     while (*budget && stall < kSlowStall) {
         --*budget;
         const u64 g = ld_acq(G);
@@ -164,12 +175,16 @@ static __device__ __noinline__ bool slow_faa(const gq_ring_view& R, int side, u3
             continue;
         }
         u64 l = ld_acq(L);
-        if ((l & kLFin) || !req_live(R, r, seq)) return false;
+        if ((l & kLFin) || !req_live(R, r, seq)) {
+            flush();
+            return false;
+        }
         const u64 c = g_cnt(g);
         u64 lc = l_cnt(l);
         if (!(l & kLInc)) {
             if (lc != *v) {               // another helper already moved r to a new ticket
                 *v = lc;
+                flush();
                 return true;
             }
             const u64 prop = (c << 2) | kLInc;   // r's ticket *v failed: propose c
@@ -196,10 +211,14 @@ static __device__ __noinline__ bool slow_faa(const gq_ring_view& R, int side, u3
                 if (cas(G, cur, cur & ~kGThrMask)) break;
             }
             *v = c;
+            flush();
             return true;
         }
-        if (q.scratch) atomicAdd(q.scratch + kStatGlobalCasFail, 1ull);
+        ++lost;
+        nap = nap ? (nap < kSlowNapMax ? 2 * nap : kSlowNapMax) : kSlowNapMin;
+        __nanosleep(nap);
     }
+    flush();
     latch_error(q.err, GQ_ERR_TIMEOUT);
     return false;
 }

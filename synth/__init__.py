@@ -192,6 +192,58 @@ def rmat_csr(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19
     return _csr_from_pairs(n, np.concatenate([src, dst]), np.concatenate([dst, src]))
 
 
+def _as_i64(x: int) -> int:
+    """The signed 64-bit integer with the same bits as the unsigned x."""
+    x &= 0xFFFFFFFFFFFFFFFF
+    return x - (1 << 64) if x >> 63 else x
+
+
+def splitmix64_torch(seed: int, ctr):
+    """SplitMix64 on a torch int64 tensor of counters (any device): the same
+    bits as ``splitmix64`` (two's-complement wrap-around for the 64-bit
+    products, logical right shifts by masking)."""
+    import torch
+    z = ctr + 1
+    z = z * _as_i64(int(GOLDEN)) + _as_i64(seed)
+    z = (z ^ ((z >> 30) & ((1 << 34) - 1))) * _as_i64(int(_M1))
+    z = (z ^ ((z >> 27) & ((1 << 37) - 1))) * _as_i64(int(_M2))
+    return z ^ ((z >> 31) & ((1 << 33) - 1))
+
+
+def rmat_csr_torch(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+                   seed: int = 0, device="cpu", chunk: int = 1 << 24):
+    """The graph of ``rmat_csr`` generated with torch tensor operations on
+    `device` (a GPU makes the large serving pools quick to build).  Returns
+    (offsets int64 [n+1], adj int32 [m]) as torch tensors on `device`; the
+    values equal rmat_csr's (uint64 offsets, uint32 ids)."""
+    import torch
+    n = 1 << scale
+    m = edge_factor * n
+    t1, t2, t3 = int(a * 2**32), int((a + b) * 2**32), int((a + b + c) * 2**32)
+    srcs, dsts = [], []
+    for lo in range(0, m, chunk):
+        e = torch.arange(lo, min(m, lo + chunk), dtype=torch.int64, device=device)
+        src = torch.zeros_like(e)
+        dst = torch.zeros_like(e)
+        for lvl in range(scale):
+            r = (splitmix64_torch(seed, e * scale + lvl) >> 32) & 0xFFFFFFFF
+            bit = 1 << (scale - 1 - lvl)
+            src |= torch.where(r >= t2, bit, 0)
+            dst |= torch.where(((r >= t1) & (r < t2)) | (r >= t3), bit, 0)
+        keep = src != dst
+        srcs.append(src[keep])
+        dsts.append(dst[keep])
+    src = torch.cat(srcs)
+    dst = torch.cat(dsts)
+    key = torch.unique(torch.cat([(src << 32) | dst, (dst << 32) | src]))   # sorted, duplicate-free
+    s = key >> 32
+    adj = (key & 0xFFFFFFFF).to(torch.int32)
+    counts = torch.bincount(s, minlength=n)
+    offsets = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    offsets[1:] = torch.cumsum(counts, 0)
+    return offsets, adj
+
+
 def bfs_sources(offsets: np.ndarray, seed: int, count: int = 3) -> np.ndarray:
     """Source vertex 0 plus ``count`` seeded non-isolated vertices."""
     n = len(offsets) - 1

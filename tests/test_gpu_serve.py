@@ -178,3 +178,34 @@ def test_full_size_pool_sampled(mode):
     for i in sorted(sample):
         want = oracle.bfs(host[gid[i]][0], host[gid[i]][1], int(src[i]))
         assert (outs[i].cpu().numpy().view(np.uint32) == want).all(), i
+
+
+def test_device_generated_graphs_equal_host_graphs():
+    for scale, seed in ((12, 5), (15, 2026007)):
+        o1, a1 = synth.rmat_csr_fast(scale, seed=seed)
+        o2, a2 = synth.rmat_csr_torch(scale, seed=seed, device="cuda")
+        assert (o2.cpu().numpy() == o1.astype(np.int64)).all()
+        assert (a2.cpu().numpy() == a1.view(np.int32)).all()
+
+
+def test_thousand_graph_pool_wfq_at_3k_rps():
+    """The serving workload at its stated size: a pool of 1000 R-MAT graphs of
+    scales 10..20 (generated on the device), Poisson arrivals at 3000 req/s,
+    G-WFQ in adaptive mode under the 32 GiB budget: every request completes,
+    the admitted state never exceeds the budget, and a sample of requests (the
+    largest graphs among them) has the oracle's distances."""
+    scales = synth.rmat_pool_scales(1000, 10, 20, 2026)
+    dev = [synth.rmat_csr_torch(int(s), seed=2026 * 1000 + i, device="cuda") for i, s in enumerate(scales)]
+    offs = [o.cpu().numpy().view(np.uint64) for o, _ in dev]
+    gid, src, arr = synth.serving_requests(offs, 600, 3000.0, seed=5)
+    order = np.argsort(-scales[gid], kind="stable")
+    sample = set(order[:3].tolist()) | set(range(0, 600, 150))
+    outs = [torch.empty(len(offs[g]) - 1, dtype=torch.int32, device="cuda") if i in sample else None
+            for i, g in enumerate(gid)]
+    r = gq.gq_serve("wfq", dev, gid, src, arr, mode="adaptive", cluster_blocks=8, budget_bytes=32 << 30, outs=outs)
+    assert (r["latency_s"] >= 0).all()
+    assert r["peak_state_bytes"] <= 32 << 30
+    for i in sorted(sample):
+        g = gid[i]
+        want = oracle.bfs(offs[g], dev[g][1].cpu().numpy().view(np.uint32), int(src[i]))
+        assert (outs[i].cpu().numpy().view(np.uint32) == want).all(), i

@@ -90,3 +90,17 @@ def test_serving_requests_poisson_and_valid_sources():
         assert off[v + 1] > off[v]                        # a non-isolated source
     g2, s2, a2 = synth.serving_requests(offs, 20000, 1000.0, seed=11)
     assert (g2 == gid).all() and (s2 == src).all() and (a2 == arr).all()
+
+
+def test_torch_rmat_generator_matches_host_generator():
+    # the device-capable generator (torch ops, wrap-around int64 products) gives the
+    # same graph bits as the host generators
+    import torch
+    x = torch.arange(4096, dtype=torch.int64) * 7919
+    assert (synth.splitmix64_torch(1234567, x).numpy().view(np.uint64)
+            == synth.splitmix64(1234567, x.numpy().astype(np.uint64))).all()
+    for scale, seed in ((8, 3), (11, 2026000)):
+        o1, a1 = synth.rmat_csr_fast(scale, seed=seed)
+        o2, a2 = synth.rmat_csr_torch(scale, seed=seed, chunk=1 << 10)   # several chunks
+        assert (o2.numpy() == o1.astype(np.int64)).all()
+        assert (a2.numpy() == a1.view(np.int32)).all()
