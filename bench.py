@@ -37,13 +37,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "queue Mops/s (enq+deq) vs threads; % of measured L2-atomic peak; serving p99"
 CAPACITY = 1 << 20
-# DRAM bytes (read + write) per launch of each run kernel at the headline size, from one ncu
-# capture of `bench.py --steps 1 --warmup 3 --no-sweep --no-e2e --no-cpu --no-apps --no-batched
-# --no-serving` with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass; profiles/).
-# Set to None whenever the kernels change.
-# G-WFQ-YMC: None since its slow-path candidate-search bound changed after the last capture
-# (987250688 + 825881088 bytes then; the bench's launches do not reach that path).
-NCU_TRAFFIC = {"lfq": 46698240 + 5093632, "wfq": 63643648 + 167041024, "ymc": None}
+# DRAM bytes (read + write) per launch of each run kernel at the headline size.  G-WFQ-YMC: one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one kernel, one launch) of the
+# 2^18-thread case of the same workload, `bench.py --threads 262144 --steps 1 --warmup 1
+# --no-sweep --no-e2e --no-cpu --no-apps --no-batched --no-serving --kinds ymc`: 247732480 +
+# 174174208 bytes for 26.2 M operations (each ticket's cell touched once), scaled by the 4x
+# operations of the headline launch (profiles/traffic_k_run_mixed_2p18.md).  The ring queues'
+# traffic is their workspace read once and does not scale with the operations, so it is not
+# extrapolated here.  Set an entry to None whenever that kernel changes.
+NCU_TRAFFIC = {"lfq": None, "wfq": None, "ymc": 4 * (247732480 + 174174208)}
 
 
 def parse():
