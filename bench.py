@@ -663,6 +663,11 @@ def main():
     e2e = None
     if not args.no_e2e:
         n = CAPACITY
+        # queues of their own, sized for the batch (G-WFQ-YMC: a pool of 3 x 2^20 cells for the batch's 2^21
+        # tickets, not the headline's 1.3 x 10^8, whose reset alone would clear 3 GB per step);
+        # the batch kernels run at most one resident wave of threads
+        eq = {k: gq.Queue(k, CAPACITY if k != "ymc" else 3 * CAPACITY, 8, max_threads=1 << 20)
+              for k in kinds}
         streams = {k: torch.cuda.Stream(device=dev) for k in kinds}
         host_items = torch.arange(1, n + 1, dtype=torch.int64).pin_memory()
         bufs = {k: {"out": torch.empty(n, dtype=torch.int64).pin_memory(),
@@ -676,10 +681,10 @@ def main():
             for k in kinds:
                 b = bufs[k]
                 with torch.cuda.stream(streams[k]):
-                    queues[k].reset()
+                    eq[k].reset()
                     b["d_items"].copy_(host_items, non_blocking=True)
-                    gq.gq_enqueue_batch(queues[k].handle, b["d_items"], n, None, b["d_cnt"][0:1])
-                    gq.gq_dequeue_batch(queues[k].handle, b["d_out"], n, None, b["d_cnt"][1:2])
+                    gq.gq_enqueue_batch(eq[k].handle, b["d_items"], n, None, b["d_cnt"][0:1])
+                    gq.gq_dequeue_batch(eq[k].handle, b["d_out"], n, None, b["d_cnt"][1:2])
                     b["out"].copy_(b["d_out"], non_blocking=True)
                     b["cnt"].copy_(b["d_cnt"], non_blocking=True)
             for k in kinds:
@@ -694,7 +699,8 @@ def main():
             tot += e2e_step()
         dt = time.perf_counter() - t0
         for k in kinds:
-            assert queues[k].sync_status() == 0
+            assert eq[k].sync_status() == 0
+            eq[k].close()
         e2e = {"value": tot / dt / 1e6, "unit": "Mops/s", "h2d_bytes_per_step": 8 * n * len(kinds),
                "d2h_bytes_per_step": (8 * n + 16) * len(kinds),
                "how": "per queue kind on its own stream: reset, pinned H2D of 2^20 items, gq_enqueue_batch, "
