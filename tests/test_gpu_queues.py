@@ -293,3 +293,38 @@ def test_capped_run_captured_in_a_graph():
         assert c[gq.GQ_CNT_ENQ_FULL] == 0 and c[gq.GQ_CNT_DEQ_EMPTY] == 0 and c[gq.GQ_CNT_ERRORS] == 0
         assert c[gq.GQ_CNT_SUM_ENQ] == c[gq.GQ_CNT_SUM_DEQ]
     assert q.sync_status() == 0
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("elem", [4, 8])
+@pytest.mark.parametrize("shift", [0, 1])
+def test_batch_api_tiles_tail_and_alignment(kind, elem, shift):
+    """The dequeue batch's tiled path (several attempts per lane, values staged in
+    shared memory and stored compacted) and its one-attempt-per-lane path (a tail
+    shorter than a tile; a status buffer not aligned for the tile's status store:
+    shift = 1 offsets items, outputs and statuses by one element) give the same
+    exactly-once result."""
+    n = (1 << 15) + 37
+    qc, _ = qcap(kind, 1 << 16, pool=1 << 18)
+    q = make_queue(kind, qc, elem, max_threads=1 << 16)
+    dt = torch.int32 if elem == 4 else torch.int64
+    base = torch.arange(1, n + 2, dtype=dt, device=DEV) * 3
+    items = base[shift:shift + n]
+    st_all = torch.full((n + 1,), -99, dtype=torch.int8, device=DEV)
+    st = st_all[shift:shift + n]
+    ok = torch.zeros(1, dtype=torch.int64, device=DEV)
+    q.enqueue(items, st, ok)
+    assert q.sync_status() == 0
+    assert int(ok.item()) == n and (st.cpu().numpy() == 0).all()
+    out_all = torch.zeros(n + 1, dtype=dt, device=DEV)
+    out = out_all[shift:shift + n]
+    st2_all = torch.full((n + 1,), -99, dtype=torch.int8, device=DEV)
+    st2 = st2_all[shift:shift + n]
+    ok2 = torch.zeros(1, dtype=torch.int64, device=DEV)
+    q.dequeue(out, st2, ok2)
+    assert q.sync_status() == 0
+    assert int(ok2.item()) == n and (st2.cpu().numpy() == 0).all()
+    assert (np.sort(out.cpu().numpy()) == np.sort(items.cpu().numpy())).all()
+    q.dequeue(out[:64], st2[:64], ok2)                  # now empty
+    assert q.sync_status() == 0
+    assert int(ok2.item()) == 0 and (st2[:64].cpu().numpy() == 2).all()
