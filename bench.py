@@ -69,6 +69,19 @@ def parse():
     return p.parse_args()
 
 
+ALL_KINDS = ["lfq", "wfq", "ymc"]
+
+
+def workload_config(args, kinds, world):
+    """The `config` object of both arms: the workload this line measures."""
+    T, K = args.threads, args.ops
+    return {"workload": "pairwise 50/50 interleaved by seed, %d threads x %d ops, capacity 2^20 uint64, queues %s"
+                        % (T, K, "+".join(kinds)),
+            "threads": T, "ops_per_thread": K, "capacity": CAPACITY, "ymc_pool_cells": int(1.25 * T * K) + (1 << 21),
+            "block": 256, "seed": args.seed, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed between timed steps (256 MiB write); queue state re-initialised inside each step"}
+
+
 def replica_totals(total_ms, succ_ops, device=None):
     """Replicas (one independent queue set per rank, no data exchange): the job's
     time is the slowest rank's and its operations are the sum over ranks."""
@@ -390,10 +403,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": "pairwise 50/50 interleaved, %d threads x %d ops, unbounded mutex deque sample"
-                                   % (Ts, K), "threads": Ts, "ops_per_thread": K, "seed": args.seed},
+            "config": workload_config(args, args.kinds.split(",") if args.kinds else ALL_KINDS, world),
             "cpu_baseline": {"value": v, "unit": "Mops/s", "cores": cores, "kind": "oracle",
-                             "sample": "first %d of %d logical threads x %d ops per step" % (Ts, T, K)},
+                             "sample": "the oracle's mutex-guarded std::deque (unbounded) on the first %d of %d "
+                                       "logical threads x %d ops of the same schedule, per step" % (Ts, T, K)},
             "e2e": {"value": v, "unit": "Mops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -725,13 +738,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "Mops/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-                "config": {"workload": "pairwise 50/50 interleaved by seed, %d threads x %d ops, capacity 2^20 "
-                                       "uint64, queues %s" % (T, K, "+".join(kinds)),
-                           "threads": T, "ops_per_thread": K, "capacity": CAPACITY, "ymc_pool_cells": ymc_pool,
-                           "block": 256, "seed": args.seed,
-                           "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "flushed between timed steps (256 MiB write); queue state re-initialised inside "
-                                 "each step"},
+                "config": workload_config(args, kinds, world),
                 "roofline": roofline, "peaks": peaks, "per_queue": per_queue, "sweep": sweep, "phases": phases,
                 "split_2p18_cap2p16": split,
                 "cpu_baseline": cpu, "e2e": e2e, "apps": apps, "batched": batched, "serving": serving,
