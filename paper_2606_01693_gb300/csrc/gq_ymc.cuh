@@ -28,8 +28,8 @@
 //   dequeue: helpers scan cells after the request's id for a candidate (a
 //            value not yet taken, or an EMPTY decision), announce it in idx and
 //            claim it with CAS deq[i] 0 -> r+2; idx = -i marks completion.
-//            Every 64th successful dequeue a thread helps one peer's dequeue
-//            request (round-robin).
+//            The dequeue that took a cell whose index is a multiple of 64
+//            inspects one peer's dequeue request: peer (cell / 64) mod k.
 // Warp-batched tickets (WaveFAA) serve the fast paths; the ticket order is the
 // same as with per-thread fetch-and-add (Lemma "WaveFAA preserves ticket order").
 //
@@ -50,7 +50,7 @@ namespace gqd {
 constexpr u64 kVBot = ~0ull;
 constexpr u64 kVTop = ~0ull - 1;
 constexpr u64 kRefBot = 0, kRefTop = 1;
-constexpr u32 kYHelpDelay = 64;   // successful dequeues per peer inspection
+constexpr u32 kYHelpDelay = 64;   // dequeue tickets per peer inspection
 constexpr u32 kYSpin = 16;      // back-to-back reads of an empty cell (its enqueuer may be on its way)
 constexpr u32 kYWaitPolls = 256; // then, if T shows the ticket taken, polls 64 ns apart
 // Cells one helper may visit in a dequeue request's candidate search.  Every
@@ -68,7 +68,6 @@ enum : int {
     kYDrIdx = 3,   // > 0 announced candidate cell, < 0 done at cell -idx
     kYEh = 4,      // private: enqueue-help peer
     kYEi = 5,      // private: id of the peer request being helped
-    kYDh = 6,      // private: dequeue-help peer (low 32 bits) and countdown (high 32 bits)
     kYWords = 16
 };
 
@@ -290,14 +289,12 @@ __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid, u64* tk = nullptr) 
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
     }
-    // the help countdown is private to this thread: load it first so that its
-    // latency overlaps the operation instead of following it
-    const u64 w = yrec(q, tid)[kYDh];         // next peer | countdown << 32
-    u64 id = 0, v = 0;
+    u64 id = 0, v = 0, help_ticket = 0;
     int res = kYUnusable;
     for (u32 p = 0; p <= q.patience_deq && res == kYUnusable; ++p) {
         const u64 i = warp_faa<MATCH, CNT>(q.ymc_head, 1, q.batch_width);
         if (!ycell_ok(q, i)) return GQ_ERR_POOL_EXHAUSTED;
+        if ((i & (kYHelpDelay - 1)) == 0) help_ticket = i;
         res = ymc_help_enq<CNT>(q, tid, i, &v);
         if (res == kYValue) {
             u64 b = kRefBot;
@@ -327,21 +324,20 @@ __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid, u64* tk = nullptr) 
         res = (v == kVTop) ? kYEmpty : kYValue;
         id = c;
     }
-    if (res == kYEmpty) return GQ_EMPTY;
-    // every kYHelpDelay-th successful dequeue, help one peer's dequeue request
-    // (round robin).  The CPU original helps after every dequeue; checking one
-    // peer every D dequeues, as G-WFQ's help delay does, keeps wait-freedom (a
-    // pending request is inspected within k * D dequeues of any thread) and
-    // saves the record load on the other D - 1 (+10 % at 2^20 threads).
-    u64* mine = yrec(q, tid);
-    const u32 left = (u32)(w >> 32);
-    if (left) {
-        mine[kYDh] = w - (1ull << 32);
-    } else {
-        const u32 peer = (u32)w;
-        mine[kYDh] = (u64)((peer + 1) % q.max_threads) | ((u64)(kYHelpDelay - 1) << 32);
+    // Help delay by ticket: the dequeue that took a cell whose index is a
+    // multiple of kYHelpDelay (whatever it returns) inspects the dequeue request
+    // of peer (cell / kYHelpDelay) mod k.  Every cell index is taken by exactly
+    // one dequeue attempt, so each peer is inspected once in every
+    // kYHelpDelay * k dequeue tickets: the bound of a per-thread countdown
+    // (k threads, one inspection per D dequeues each), without the per-thread
+    // countdown's load and store on every dequeue, which the release and
+    // acq_rel atomics of the next operations had to wait for.  (The CPU
+    // original helps after every dequeue.)
+    if (help_ticket) {
+        const u32 peer = (u32)((help_ticket / kYHelpDelay) % q.max_threads);
         if (peer != tid) ymc_help_deq(q, tid, peer);
     }
+    if (res == kYEmpty) return GQ_EMPTY;
     if (tk) *tk = id;
     *out = (T)v;
     return GQ_OK;
