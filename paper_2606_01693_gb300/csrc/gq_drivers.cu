@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256, 4) k_run(const __grid_constant__ gq_dev q
                     ++seq;
                 }
                 T x = (T)v;
-                s = queue_op<T, KIND, CNT>(q, is_enq, &x, t, tkp);
+                s = queue_op<T, KIND, CNT>(q, is_enq, &x, t, tkp, i);
                 if (is_enq) {
                     if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
                     else if (s == GQ_FULL) ++c_full;
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(256, 4) k_run_multi(const gq_dev* __restrict__
         if (t < a.ppq) {
             for (u32 i = 0; i < nops; ++i) {
                 const u64 v = (sizeof(T) == 4) ? ((L << 16) | i) : ((L << 32) | (u64)(i + 1));
-                const int s = queue_enqueue<T, KIND, true, CNT>(q, (T)v, t, tkp);
+                const int s = queue_enqueue<T, KIND, true, CNT>(q, (T)v, t, tkp, i);
                 if (s == GQ_OK) { ++c_enq_ok; s_enq += v; }
                 else if (s == GQ_FULL) ++c_full;
                 else ++c_err;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256, 4) k_run_multi(const gq_dev* __restrict__
         } else {
             for (u32 i = 0; i < nops; ++i) {
                 T x = 0;
-                const int s = queue_dequeue<T, KIND, true, CNT>(q, &x, t, tkp);
+                const int s = queue_dequeue<T, KIND, true, CNT>(q, &x, t, tkp, i);
                 if (s == GQ_OK) { ++c_deq_ok; s_deq += (u64)x; }
                 else if (s == GQ_EMPTY) ++c_empty;
                 else ++c_err;

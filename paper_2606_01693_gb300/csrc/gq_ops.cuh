@@ -15,17 +15,19 @@ namespace gqd {
 // allocated-index ring (G-LFQ, G-WFQ) or its cell (G-WFQ-YMC); an item's
 // enqueue and the dequeue that returns it get the same one.
 // CNT: the counting instantiation (per-thread event counts, see gq_atomics.cuh).
+// seq (run drivers): the index of the operation among the thread's operations
+// on this queue; G-WFQ derives its help delay from it (wfq_maybe_help).
 template <class T, int KIND, bool MATCH = false, bool CNT = false>
-__device__ __forceinline__ int queue_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
+__device__ __forceinline__ int queue_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr, u32 seq = kNoSeq) {
     if constexpr (KIND == GQ_LFQ) return lfq_enqueue<T, MATCH, CNT>(q, v, tk);
-    else if constexpr (KIND == GQ_WFQ) return wfq_enqueue<T, MATCH, CNT>(q, v, tid, tk);
+    else if constexpr (KIND == GQ_WFQ) return wfq_enqueue<T, MATCH, CNT>(q, v, tid, tk, seq);
     else return ymc_enqueue<T, MATCH, CNT>(q, v, tid, tk);
 }
 
 template <class T, int KIND, bool MATCH = false, bool CNT = false>
-__device__ __forceinline__ int queue_dequeue(const gq_dev& q, T* v, u32 tid, u64* tk = nullptr) {
+__device__ __forceinline__ int queue_dequeue(const gq_dev& q, T* v, u32 tid, u64* tk = nullptr, u32 seq = kNoSeq) {
     if constexpr (KIND == GQ_LFQ) return lfq_dequeue<T, MATCH, CNT>(q, v, tk);
-    else if constexpr (KIND == GQ_WFQ) return wfq_dequeue<T, MATCH, CNT>(q, v, tid, tk);
+    else if constexpr (KIND == GQ_WFQ) return wfq_dequeue<T, MATCH, CNT>(q, v, tid, tk, seq);
     else return ymc_dequeue<T, MATCH, CNT>(q, v, tid, tk);
 }
 
@@ -33,9 +35,9 @@ __device__ __forceinline__ int queue_dequeue(const gq_dev& q, T* v, u32 tid, u64
 // G-LFQ and G-WFQ run both on one code path (their operations mirror each
 // other over the two index rings); G-WFQ-YMC branches.
 template <class T, int KIND, bool CNT = false>
-__device__ __forceinline__ int queue_op(const gq_dev& q, bool enq, T* v, u32 tid, u64* tk = nullptr) {
+__device__ __forceinline__ int queue_op(const gq_dev& q, bool enq, T* v, u32 tid, u64* tk = nullptr, u32 seq = kNoSeq) {
     if constexpr (KIND == GQ_LFQ) return lfq_op<T, CNT>(q, enq, v, tk);
-    else if constexpr (KIND == GQ_WFQ) return wfq_op<T, CNT>(q, enq, v, tid, tk);
+    else if constexpr (KIND == GQ_WFQ) return wfq_op<T, CNT>(q, enq, v, tid, tk, seq);
     else return enq ? ymc_enqueue<T, false, CNT>(q, *v, tid, tk) : ymc_dequeue<T, false, CNT>(q, v, tid, tk);
 }
 

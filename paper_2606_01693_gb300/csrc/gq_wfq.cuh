@@ -461,12 +461,7 @@ static __device__ __noinline__ void wfq_help_request(const gq_ring_view& R, cons
 
 // Inspects the next peer record (round robin) and helps it if a request is
 // pending with matching sequence fields.
-static __device__ __noinline__ void wfq_help_peer(const gq_ring_view& R, const gq_dev& q, u32 me, u64 pv) {
-    u32 peer = (u32)(pv >> 32);
-    peer = (peer + 1) % q.max_threads;
-    if (peer == me) peer = (peer + 1) % q.max_threads;
-    R.helpc[me] = ((u64)peer << 32) | q.help_delay;
-    if (peer == me) return;
+static __device__ __noinline__ void wfq_inspect_peer(const gq_ring_view& R, const gq_dev& q, u32 me, u32 peer) {
     u64* pr = rec_of(R, peer);
     const u64 pend = ld_acq(pr + kRPending);
     if (!(pend & 1)) return;
@@ -480,10 +475,37 @@ static __device__ __noinline__ void wfq_help_peer(const gq_ring_view& R, const g
     wfq_help_request(R, q, peer, s2, (pend2 & 2) != 0, init, (u32)idx, me);
 }
 
+// The next peer after `prev` in round-robin order, skipping the caller.
+__device__ __forceinline__ u32 wfq_next_peer(const gq_dev& q, u32 me, u32 prev) {
+    u32 peer = (prev + 1) % q.max_threads;
+    if (peer == me) peer = (peer + 1) % q.max_threads;
+    return peer;
+}
+
+static __device__ __noinline__ void wfq_help_peer(const gq_ring_view& R, const gq_dev& q, u32 me, u64 pv) {
+    // a cursor never used yet (zeroed at reset) starts the round robin at the
+    // caller's own id, so that threads do not all inspect the same peers at once
+    const u32 peer = wfq_next_peer(q, me, pv ? (u32)(pv >> 32) : me);
+    R.helpc[me] = ((u64)peer << 32) | q.help_delay;
+    if (peer != me) wfq_inspect_peer(R, q, me, peer);
+}
+
 // Help delay D (Section III-C): every D operations a thread inspects one peer
-// record.  The countdown is owner-only state in a compact per-thread array
-// (plain accesses; the 32 cursors of a warp share one 256-byte span).
-__device__ __forceinline__ void wfq_maybe_help(const gq_ring_view& R, const gq_dev& q, u32 me) {
+// record, round robin from its own id.  Callers that know the index `seq` of
+// this operation among the thread's operations on this ring (the run drivers)
+// pass it: the operation inspects peer me + 1 + seq / D when seq is a multiple
+// of D, and no per-thread state is read or written.  Otherwise (kNoSeq) the
+// countdown is owner-only state in a compact per-thread array (plain accesses;
+// the 32 cursors of a warp share one 256-byte span).
+constexpr u32 kNoSeq = 0xFFFFFFFFu;
+__device__ __forceinline__ void wfq_maybe_help(const gq_ring_view& R, const gq_dev& q, u32 me, u32 seq = kNoSeq) {
+    if (seq != kNoSeq) {
+        if (seq % q.help_delay == 0) {
+            const u32 peer = wfq_next_peer(q, me, (u32)((me + (u64)(seq / q.help_delay)) % q.max_threads));
+            if (peer != me) wfq_inspect_peer(R, q, me, peer);
+        }
+        return;
+    }
     const u64 pv = R.helpc[me];
     const u32 countdown = (u32)pv;
     if (countdown > 1 && countdown <= q.help_delay) {
@@ -518,8 +540,8 @@ static __device__ __noinline__ u64 wfq_slow_request(const gq_ring_view& R, const
 // recorder): the ticket the index was installed at, fast or slow.
 template <bool MATCH, bool CNT = false>
 __device__ int wfq_ring_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u32 me, u32 patience,
-                            u64* tk = nullptr) {
-    wfq_maybe_help(R, q, me);
+                            u64* tk = nullptr, u32 seq = kNoSeq) {
+    wfq_maybe_help(R, q, me, seq);
     u64 t = 0;
     for (u32 p = 0; p < patience; ++p) {
         if (wfq_try_enq<MATCH, CNT>(R, q, idx, &t) == kTryOk) {
@@ -552,9 +574,9 @@ __device__ int wfq_ring_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u32
 // (nullable): the ticket the index was taken at.
 template <bool MATCH, bool CNT = false>
 __device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u32 me, u32 patience,
-                            u64* tk = nullptr) {
+                            u64* tk = nullptr, u32 seq = kNoSeq) {
     if (ld_rlx(R.threshold) < 0) return GQ_EMPTY;
-    wfq_maybe_help(R, q, me);
+    wfq_maybe_help(R, q, me, seq);
     u64 h = 0;
     for (u32 p = 0; p < patience; ++p) {
         const int s = wfq_try_deq<MATCH, CNT>(R, q, idx, &h);
@@ -586,14 +608,16 @@ __device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u3
 }
 
 // tk (nullable, test recorder): the aq ticket of the operation.
+// seq (run drivers): the index of this operation among the thread's
+// operations on this queue (see wfq_maybe_help); kNoSeq otherwise.
 template <class T, bool MATCH, bool CNT = false>
-__device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
+__device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr, u32 seq = kNoSeq) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
     }
     u32 i;
-    int s = wfq_ring_deq<MATCH, CNT>(q.fq, q, &i, tid, q.patience_deq);
+    int s = wfq_ring_deq<MATCH, CNT>(q.fq, q, &i, tid, q.patience_deq, nullptr, seq);
     if (s == GQ_EMPTY) return GQ_FULL;
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {
@@ -601,31 +625,31 @@ __device__ int wfq_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
         return GQ_ERR_INVALID;
     }
     data_store<T>(q, i, v);
-    return wfq_ring_enq<MATCH, CNT>(q.aq, q, i, tid, q.patience_enq, tk);
+    return wfq_ring_enq<MATCH, CNT>(q.aq, q, i, tid, q.patience_enq, tk, seq);
 }
 
 template <class T, bool MATCH, bool CNT = false>
-__device__ int wfq_dequeue(const gq_dev& q, T* v, u32 tid, u64* tk = nullptr) {
+__device__ int wfq_dequeue(const gq_dev& q, T* v, u32 tid, u64* tk = nullptr, u32 seq = kNoSeq) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
     }
     u32 i;
-    int s = wfq_ring_deq<MATCH, CNT>(q.aq, q, &i, tid, q.patience_deq, tk);
+    int s = wfq_ring_deq<MATCH, CNT>(q.aq, q, &i, tid, q.patience_deq, tk, seq);
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {
         latch_error(q.err, GQ_ERR_INVALID);
         return GQ_ERR_INVALID;
     }
     *v = data_load<T>(q, i);
-    s = wfq_ring_enq<MATCH, CNT>(q.fq, q, i, tid, q.patience_enq);
+    s = wfq_ring_enq<MATCH, CNT>(q.fq, q, i, tid, q.patience_enq, nullptr, seq);
     return s == GQ_OK ? GQ_OK : s;
 }
 
 // Enqueue or dequeue on one code path (see lfq_op): the rings are chosen per
 // lane, so mixed warps run both kinds of operation together.
 template <class T, bool CNT = false>
-__device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid, u64* tk = nullptr) {
+__device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid, u64* tk = nullptr, u32 seq = kNoSeq) {
     if (tid >= q.max_threads) {
         latch_error(q.err, GQ_ERR_TOO_MANY_THREADS);
         return GQ_ERR_TOO_MANY_THREADS;
@@ -633,7 +657,7 @@ __device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid, u64* tk = nullpt
     const gq_ring_view& from = enq ? q.fq : q.aq;
     const gq_ring_view& to = enq ? q.aq : q.fq;
     u32 i;
-    int s = wfq_ring_deq<true, CNT>(from, q, &i, tid, q.patience_deq, enq ? nullptr : tk);
+    int s = wfq_ring_deq<true, CNT>(from, q, &i, tid, q.patience_deq, enq ? nullptr : tk, seq);
     if (s == GQ_EMPTY) return enq ? GQ_FULL : GQ_EMPTY;
     if (s != GQ_OK) return s;
     if (i >= q.capacity) {
@@ -642,7 +666,7 @@ __device__ int wfq_op(const gq_dev& q, bool enq, T* v, u32 tid, u64* tk = nullpt
     }
     if (enq) data_store<T>(q, i, *v);
     else *v = data_load<T>(q, i);
-    return wfq_ring_enq<true, CNT>(to, q, i, tid, q.patience_enq, enq ? tk : nullptr);
+    return wfq_ring_enq<true, CNT>(to, q, i, tid, q.patience_enq, enq ? tk : nullptr, seq);
 }
 
 }  // namespace gqd
