@@ -89,6 +89,14 @@ typedef struct {
      * Algorithm 1; waiting measured no better on the benchmark workloads);
      * GQ_DUE_WAIT_OFF = no waiting either.  At most 65536. */
     uint32_t due_wait;
+    /* G-WFQ patience stretch: a ring operation that has used its patience
+     * while requests of the same ring are already waiting on the slow path
+     * keeps trying the fast path, up to patience * patience_stretch attempts
+     * in all, before it publishes its own request (each attempt still bounded,
+     * so operations stay wait-free with the larger bound).  1 = off (the
+     * plain Section III-C rule).  0 = default 64.  At most 4096. */
+    uint32_t patience_stretch;
+    uint32_t reserved_opt;   /* must be 0 */
     /* Initial value of every ticket counter (tests of counter wrap-around).
      * Must be a multiple of 2 * capacity.  Default 0. */
     uint64_t start_ticket;
@@ -103,6 +111,7 @@ typedef struct {
     unsigned long long* rec;        /* G-WFQ request records (NULL for G-LFQ)      */
     unsigned long long* owner;      /* G-WFQ: record id that enqueues each index    */
     unsigned long long* helpc;      /* G-WFQ: per-thread help cursor <peer, countdown> */
+    unsigned long long* slow_pending; /* G-WFQ: requests published, not yet retired */
 } gq_ring_view;
 
 typedef struct {
@@ -116,6 +125,8 @@ typedef struct {
     uint32_t ring_order;            /* log2(2n)                                    */
     uint32_t backoff_ns;            /* sleep after a failed ticket attempt          */
     uint32_t due_wait;              /* due-install polls of a ring dequeuer (0: none) */
+    uint32_t patience_stretch;      /* G-WFQ: fast attempts x this while the slow path is busy */
+    uint32_t reserved1;
     uint64_t capacity;              /* ring: n; YMC: pool cells                    */
     uint64_t slot_mask;             /* 2n - 1                                      */
     uint64_t cycle_mask;            /* R - 1, R = 2^cycle_bits                     */
@@ -202,7 +213,10 @@ int gq_device_view(gq_handle h, gq_dev* out);
  *                        request
  *   aq_head .. fq_tail   current ticket counters: G-LFQ the raw words, G-WFQ
  *                        the Counter field of each Global word, G-WFQ-YMC H
- *                        and T in aq_head / aq_tail (fq_* zero) */
+ *                        and T in aq_head / aq_tail (fq_* zero)
+ *   aq_slow_pending, fq_slow_pending  G-WFQ with a patience stretch above
+ *                        1: requests published on each ring and not yet
+ *                        retired (0 between kernels; otherwise zero) */
 typedef struct {
     unsigned long long slow_requests;
     unsigned long long helps;
@@ -211,6 +225,7 @@ typedef struct {
     unsigned long long slow_rounds_head;
     unsigned long long max_help_iterations;
     unsigned long long aq_head, aq_tail, fq_head, fq_tail;
+    unsigned long long aq_slow_pending, fq_slow_pending;
 } gq_stats;
 int gq_get_stats(gq_handle h, gq_stats* out);
 

@@ -59,6 +59,7 @@ class gq_options(ctypes.Structure):
                 ("patience_deq", ctypes.c_uint32), ("patience_set", ctypes.c_uint32),
                 ("help_delay", ctypes.c_uint32), ("batch_width", ctypes.c_uint32),
                 ("backoff_ns", ctypes.c_uint32), ("due_wait", ctypes.c_uint32),
+                ("patience_stretch", ctypes.c_uint32), ("reserved_opt", ctypes.c_uint32),
                 ("start_ticket", ctypes.c_uint64)]
 
 
@@ -232,7 +233,8 @@ class gq_stats(ctypes.Structure):
                 ("global_cas_failures", ctypes.c_uint64), ("slow_rounds_tail", ctypes.c_uint64),
                 ("slow_rounds_head", ctypes.c_uint64), ("max_help_iterations", ctypes.c_uint64),
                 ("aq_head", ctypes.c_uint64), ("aq_tail", ctypes.c_uint64), ("fq_head", ctypes.c_uint64),
-                ("fq_tail", ctypes.c_uint64)]
+                ("fq_tail", ctypes.c_uint64), ("aq_slow_pending", ctypes.c_uint64),
+                ("fq_slow_pending", ctypes.c_uint64)]
 
 
 def gq_get_stats(h: int) -> dict:
@@ -391,11 +393,12 @@ class MultiQueue:
         self.prepare()
 
     def prepare(self, batch_width: int = 0, backoff_ns: int | None = None, patience=None, help_delay: int = 0,
-                due_wait: int = 0, stream=None):
+                due_wait: int = 0, patience_stretch: int = 0, stream=None):
         tune = None
-        if batch_width or backoff_ns is not None or patience is not None or help_delay or due_wait:
+        if (batch_width or backoff_ns is not None or patience is not None or help_delay or due_wait
+                or patience_stretch):
             tune = gq_options(batch_width=batch_width, backoff_ns=backoff_ns or 0, help_delay=help_delay,
-                              due_wait=due_wait)
+                              due_wait=due_wait, patience_stretch=patience_stretch)
             if patience is not None:
                 tune.patience_enq, tune.patience_deq, tune.patience_set = patience[0], patience[1], 1
         gq_multi_prepare(self.handles, self.views, tune, stream)

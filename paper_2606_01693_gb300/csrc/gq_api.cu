@@ -36,6 +36,9 @@ int resolve(int kind, uint64_t cap, uint32_t elem, uint32_t max_threads, const g
     if (o.due_wait == GQ_DUE_WAIT_OFF) o.due_wait = 0;
     else if (o.due_wait > 65536) return GQ_ERR_INVALID;
     if (kind == GQ_YMC) o.due_wait = 0;
+    if (o.reserved_opt != 0 || o.patience_stretch > 4096) return GQ_ERR_INVALID;
+    if (kind != GQ_WFQ) o.patience_stretch = 1;
+    else if (o.patience_stretch == 0) o.patience_stretch = 64;
     if (kind == GQ_YMC) {
         if (cap < 2 || cap > (1ull << 40)) return GQ_ERR_INVALID;
         if (max_threads > (1u << 24) - 1) return GQ_ERR_TOO_MANY_THREADS;   // 24-bit thread field of cell references
@@ -131,6 +134,10 @@ __global__ void k_reset_ctrl(gq_dev q, u64 base_ticket) {
     }
     *q.aq.threshold = -1;
     *q.fq.threshold = (long long)(3 * n) - 1;
+    if (q.kind == GQ_WFQ) {
+        *q.aq.slow_pending = 0;
+        *q.fq.slow_pending = 0;
+    }
 }
 
 // Ring slots: aq empty (cycle c0 - 1); fq holds 0..n-1 at cycle c0.
@@ -386,6 +393,7 @@ extern "C" int gq_create(int kind, uint64_t capacity, uint32_t elem_bytes, uint3
     d.batch_width = o.batch_width;
     d.backoff_ns = o.backoff_ns;
     d.due_wait = o.due_wait;
+    d.patience_stretch = o.patience_stretch;
     d.capacity = capacity;
     if (kind != GQ_YMC) {
         d.ring_order = d.log2n + 1;
@@ -421,6 +429,8 @@ extern "C" int gq_create(int kind, uint64_t capacity, uint32_t elem_bytes, uint3
             d.fq.owner = at<unsigned long long>(b, h->lay.fq_owner);
             d.aq.helpc = at<unsigned long long>(b, h->lay.aq_helpc);
             d.fq.helpc = at<unsigned long long>(b, h->lay.fq_helpc);
+            d.aq.slow_pending = at<unsigned long long>(b, h->lay.ctrl + kCtlAqSlow * kCtlStride);
+            d.fq.slow_pending = at<unsigned long long>(b, h->lay.ctrl + kCtlFqSlow * kCtlStride);
         }
     }
     s = gq_reset(h, stream);
@@ -504,6 +514,11 @@ extern "C" int gq_get_stats(gq_handle h, gq_stats* out) {
         if (!src[i]) continue;
         if (cudaMemcpy(dst[i], src[i], 8, cudaMemcpyDeviceToHost) != cudaSuccess) return GQ_ERR_CUDA;
         if (d.kind == GQ_WFQ) *dst[i] >>= kGThrBits;          // the Counter field of a Global word
+    }
+    if (d.kind == GQ_WFQ) {
+        if (cudaMemcpy(&out->aq_slow_pending, d.aq.slow_pending, 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(&out->fq_slow_pending, d.fq.slow_pending, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return GQ_ERR_CUDA;
     }
     return GQ_OK;
 }

@@ -335,7 +335,7 @@ int launch_multi(const gq_dev* views, const gq_multi_args& g, cudaStream_t st) {
 }
 
 __global__ void k_multi_tune(gq_dev* views, u32 n, u32 width, u32 backoff, u32 set_patience, u32 pe, u32 pd,
-                             u32 delay, u32 due) {
+                             u32 delay, u32 due, u32 stretch) {
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (width) views[i].batch_width = width;
@@ -345,6 +345,7 @@ __global__ void k_multi_tune(gq_dev* views, u32 n, u32 width, u32 backoff, u32 s
         views[i].patience_deq = pd;
     }
     if (delay && views[i].kind == GQ_WFQ) views[i].help_delay = delay;
+    if (stretch && views[i].kind == GQ_WFQ) views[i].patience_stretch = stretch;
     // due-install wait: 0 keeps the queue's own, GQ_DUE_WAIT_OFF turns it off
     if (due && views[i].kind != GQ_YMC) views[i].due_wait = (due == GQ_DUE_WAIT_OFF) ? 0u : due;
 }
@@ -361,6 +362,7 @@ extern "C" int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void*
     if (tune && tune->batch_width && (tune->batch_width > 32 || (tune->batch_width & (tune->batch_width - 1))))
         return GQ_ERR_INVALID;
     if (tune && tune->due_wait > 65536 && tune->due_wait != GQ_DUE_WAIT_OFF) return GQ_ERR_INVALID;
+    if (tune && (tune->patience_stretch > 4096 || tune->reserved_opt != 0)) return GQ_ERR_INVALID;
     // a new G-WFQ help delay D must keep every queue within its modular-cycle bound R > D k / n + 6
     if (tune && tune->help_delay && queues[0]->dev.kind == GQ_WFQ)
         for (uint32_t i = 0; i < nqueues; ++i) {
@@ -377,7 +379,8 @@ extern "C" int gq_multi_prepare(const gq_handle* queues, uint32_t nqueues, void*
     if (tune) {
         k_multi_tune<<<(nqueues + 255) / 256, 256, 0, st>>>(v, nqueues, tune->batch_width, tune->backoff_ns,
                                                             tune->patience_set, tune->patience_enq, tune->patience_deq,
-                                                            tune->help_delay, tune->due_wait);
+                                                            tune->help_delay, tune->due_wait,
+                                                            tune->patience_stretch);
         return gq_check_launch();
     }
     return GQ_OK;

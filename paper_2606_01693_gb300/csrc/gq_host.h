@@ -33,6 +33,7 @@ enum {
     kCtlAqHead = 2, kCtlAqTail = 3, kCtlAqThr = 4,
     kCtlFqHead = 5, kCtlFqTail = 6, kCtlFqThr = 7,
     kCtlYmcTail = 8, kCtlYmcHead = 9,
+    kCtlAqSlow = 10, kCtlFqSlow = 11,
     kCtlLines = 16
 };
 

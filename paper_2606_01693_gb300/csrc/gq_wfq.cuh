@@ -515,9 +515,34 @@ __device__ __forceinline__ void wfq_maybe_help(const gq_ring_view& R, const gq_d
     wfq_help_peer(R, q, me, pv);
 }
 
+// Patience stretch: an operation that has used its patience while requests
+// of the same ring are already on the slow path keeps trying the fast path,
+// up to patience * patience_stretch attempts in all.  Each request on the
+// slow path costs rounds of SlowFAA that serialise on the ring's counter;
+// when many operations run out of patience together (more threads than
+// slots, operations that keep finding their slot taken) their requests queue
+// behind each other while fast attempts would have gone through.  The ring's
+// pending count is claimed with one fetch-and-add when it reads zero, so of
+// the operations that run out of patience at the same moment one publishes
+// and the others stretch.  The bound stays finite, so the operation stays
+// wait-free.  Returns the new attempt limit; *claimed is set when the caller
+// holds a pending count it has to publish under.
+__device__ __forceinline__ u32 wfq_stretch(const gq_ring_view& R, const gq_dev& q, u32 patience, bool* claimed) {
+    const u64 lim = (u64)patience * q.patience_stretch;
+    const u32 big = lim > 0xFFFFFFFFull ? 0xFFFFFFFFu : (u32)lim;
+    if (ld_rlx(R.slow_pending) != 0) return big;
+    if (atomicAdd(R.slow_pending, 1ull) == 0) {
+        *claimed = true;
+        return patience;
+    }
+    atomicAdd(R.slow_pending, ~0ull);   // minus one: another operation publishes first
+    return big;
+}
+
 // Publishes a request in the caller's record, helps it to completion, and
 // retires it.  Returns the final local word (FIN set) or 0 on timeout.
-static __device__ __noinline__ u64 wfq_slow_request(const gq_ring_view& R, const gq_dev& q, u32 me, bool enq, u64 init, u32 idx) {
+static __device__ __noinline__ u64 wfq_slow_request(const gq_ring_view& R, const gq_dev& q, u32 me, bool enq, u64 init, u32 idx,
+                                                    bool claimed) {
     u64* rec = rec_of(R, me);
     const u64 seq = ld_rlx(rec + kRSeq1);
     u64* L = rec + (enq ? kRLocalTail : kRLocalHead);
@@ -528,10 +553,12 @@ static __device__ __noinline__ u64 wfq_slow_request(const gq_ring_view& R, const
     st_rel(rec + kRSeq2, seq);
     st_rel(rec + kRPending, 1ull | (enq ? 2ull : 0ull));
     if (q.scratch) atomicAdd(q.scratch + kStatSlowRequests, 1ull);
+    if (q.patience_stretch > 1 && !claimed) atomicAdd(R.slow_pending, 1ull);
     wfq_help_request(R, q, me, seq, enq, init, idx, me);
     const u64 l = ld_acq(L);
     st_rel(rec + kRPending, 0);
     st_rel(rec + kRSeq1, seq + 1);
+    if (q.patience_stretch > 1) atomicAdd(R.slow_pending, ~0ull);   // minus one
     return (l & kLFin) ? l : 0;
 }
 
@@ -543,16 +570,21 @@ __device__ int wfq_ring_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u32
                             u64* tk = nullptr, u32 seq = kNoSeq) {
     wfq_maybe_help(R, q, me, seq);
     u64 t = 0;
-    for (u32 p = 0; p < patience; ++p) {
+    bool stretched = false, claimed = false;
+    for (u32 p = 0, lim = patience; p < lim; ++p) {
         if (wfq_try_enq<MATCH, CNT>(R, q, idx, &t) == kTryOk) {
             if (tk) *tk = t;
             return GQ_OK;
         }
         if (q.backoff_ns) __nanosleep(q.backoff_ns);
+        if (p + 1 == lim && !stretched && q.patience_stretch > 1) {
+            stretched = true;
+            lim = wfq_stretch(R, q, patience, &claimed);
+        }
     }
     if (patience == 0) t = (g_cnt(ld_rlx(R.tail)) - 1) & kCntMask;   // a ticket value r never held
     oc_add<CNT>(kOcSlow);
-    const u64 l = wfq_slow_request(R, q, me, true, t, idx);
+    const u64 l = wfq_slow_request(R, q, me, true, t, idx, claimed);
     if (!l) {
         latch_error(q.err, GQ_ERR_TIMEOUT);
         return GQ_ERR_TIMEOUT;
@@ -578,7 +610,8 @@ __device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u3
     if (ld_rlx(R.threshold) < 0) return GQ_EMPTY;
     wfq_maybe_help(R, q, me, seq);
     u64 h = 0;
-    for (u32 p = 0; p < patience; ++p) {
+    bool stretched = false, claimed = false;
+    for (u32 p = 0, lim = patience; p < lim; ++p) {
         const int s = wfq_try_deq<MATCH, CNT>(R, q, idx, &h);
         if (s == kTryOk) {
             if (tk) *tk = h;
@@ -586,10 +619,14 @@ __device__ int wfq_ring_deq(const gq_ring_view& R, const gq_dev& q, u32* idx, u3
         }
         if (s == kTryEmpty) return GQ_EMPTY;
         if (q.backoff_ns) __nanosleep(q.backoff_ns);
+        if (p + 1 == lim && !stretched && q.patience_stretch > 1) {
+            stretched = true;
+            lim = wfq_stretch(R, q, patience, &claimed);
+        }
     }
     if (patience == 0) h = (g_cnt(ld_rlx(R.head)) - 1) & kCntMask;
     oc_add<CNT>(kOcSlow);
-    const u64 l = wfq_slow_request(R, q, me, false, h, 0);
+    const u64 l = wfq_slow_request(R, q, me, false, h, 0, claimed);
     if (!l) {
         latch_error(q.err, GQ_ERR_TIMEOUT);
         return GQ_ERR_TIMEOUT;

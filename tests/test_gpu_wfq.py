@@ -38,13 +38,15 @@ def test_slow_path_sequential_bit_exact(cap, seed):
     assert st["slow_requests"] >= len(kinds)
 
 
-@pytest.mark.parametrize("patience", [0, 1])
+@pytest.mark.parametrize("patience,stretch", [(0, 0), (1, 1), (1, 0)])
 @pytest.mark.parametrize("help_delay", [1, 64])
-def test_slow_path_concurrent_mixed(patience, help_delay):
+def test_slow_path_concurrent_mixed(patience, stretch, help_delay):
+    # stretch 0 = the default patience stretch (fast attempts go on while
+    # requests of the ring are pending), 1 = off
     T, K = 1 << 12, 40
     sched = synth.mixed_schedule_bits(17, T, K)
     q = make_queue("wfq", 1 << 10, 8, max_threads=T, help_delay=help_delay,
-                   patience_enq=patience, patience_deq=patience)
+                   patience_enq=patience, patience_deq=patience, patience_stretch=stretch)
     r = run_log(q, gq.GQ_RUN_MIXED, T, K, sched=sched)
     left = drain(q, 1 << 10)
     rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
@@ -84,6 +86,25 @@ def test_slow_path_tiny_histories(patience):
                                   r["call"].reshape(-1)[m], r["end"].reshape(-1)[m], cap=cap)
         assert res == 1, (trial, r)
         q.close()
+
+
+@pytest.mark.parametrize("stretch", [1, 4, 64])
+@pytest.mark.parametrize("frac", [0.1, 0.5, 0.9])
+def test_patience_stretch_split_oversubscribed(stretch, frac):
+    # more threads than slots, small patience: operations run out of patience
+    # while requests are already pending, the case the stretch is for; every
+    # stretch setting must keep the run log valid and leave no request pending
+    T, total, cap = 1 << 13, 300000, 1 << 8
+    q = make_queue("wfq", cap, 8, max_threads=T, patience_enq=2, patience_deq=4, help_delay=16,
+                   patience_stretch=stretch)
+    r = run_log(q, gq.GQ_RUN_SPLIT, T, producers=int(frac * T), total_ops=total)
+    left = drain(q, cap)
+    rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
+    assert rep["violations"] == 0, str(rep)
+    assert r["counts"][gq.GQ_CNT_ERRORS] == 0
+    st = q.stats()
+    assert st["slow_requests"] > 0
+    assert st["aq_slow_pending"] == 0 and st["fq_slow_pending"] == 0, st
 
 
 def test_delay_injection_many_threads():

@@ -66,9 +66,21 @@ def test_wfq_cycle_soundness_bound():
 
 def test_bad_options_rejected():
     for o in (gq.gq_options(batch_width=3), gq.gq_options(batch_width=64), gq.gq_options(cycle_bits=32),
-              gq.gq_options(start_ticket=5)):
+              gq.gq_options(start_ticket=5), gq.gq_options(patience_stretch=4097),
+              gq.gq_options(reserved_opt=1)):
         with pytest.raises(gq.GqError):
             gq.gq_workspace_bytes(gq.GQ_LFQ, 16, 8, 1, o)
+    # the patience stretch is a G-WFQ option; its bound holds for every kind
+    assert gq.gq_workspace_bytes(gq.GQ_WFQ, 16, 8, 1, gq.gq_options(patience_stretch=4096)) > 0
+    with pytest.raises(gq.GqError):
+        gq.gq_workspace_bytes(gq.GQ_WFQ, 16, 8, 1, gq.gq_options(patience_stretch=4097))
+
+
+def test_options_layout_matches_header():
+    # gq_options as include/gq.h declares it: nine 32-bit fields, then the 64-bit start ticket
+    assert ctypes.sizeof(gq.gq_options) == 48
+    assert gq.gq_options.start_ticket.offset == 40
+    assert gq.gq_options.patience_stretch.offset == 32
 
 
 def test_workspace_grows_with_capacity_and_records():
