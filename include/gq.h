@@ -139,9 +139,10 @@ typedef struct {
     /* G-WFQ-YMC */
     unsigned long long* ymc_tail;   /* T counter                                   */
     unsigned long long* ymc_head;   /* H counter                                   */
-    unsigned long long* cell_val;   /* pool cell values                            */
+    unsigned long long* cell_val;   /* pool cell values: cell i at cell_val[2 i]   */
     unsigned long long* cell_enq;   /* pool cell enqueue-request references        */
-    unsigned long long* cell_deq;   /* pool cell dequeue-request references        */
+    unsigned long long* cell_deq;   /* dequeue references: cell i at cell_deq[2 i]
+                                       (= cell_val[2 i + 1], one 16-byte pair)     */
     unsigned long long* ymc_rec;    /* per-thread handles and requests             */
 } gq_dev;
 

@@ -1,6 +1,7 @@
 // libgq host API: workspace layout, create / destroy / reset, and the
 // host-launched batch enqueue / dequeue kernels (declared in include/gq.h).
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <stdlib.h>
 #include <string.h>
 
@@ -80,9 +81,11 @@ gq_layout make_layout(int kind, uint64_t cap, uint32_t elem, uint32_t max_thread
     off += kCtlLines * kCtlStride;
     if (kind == GQ_YMC) {
         const uint64_t cells = cap + 1;  // tickets start at 1; cell index = ticket
-        off = align_up(off, 256); L.cell_val = off; off += cells * 8;
+        // value and dequeue reference of a cell side by side in one 16-byte
+        // pair (a dequeue reads one and CASes the other: one L2 sector);
+        // enqueue references, touched only by slow enqueues, apart
+        off = align_up(off, 256); L.cell_val = off; L.cell_deq = off + 8; off += cells * 16;
         off = align_up(off, 256); L.cell_enq = off; off += cells * 8;
-        off = align_up(off, 256); L.cell_deq = off; off += cells * 8;
         off = align_up(off, 256); L.ymc_rec = off; off += (uint64_t)max_threads * kYmcRecBytes;
     } else {
         off = align_up(off, 256); L.aq_slots = off; off += 2 * cap * 8;
@@ -160,6 +163,15 @@ __global__ void k_reset_slots(gq_dev q, u64 base_ticket) {
             q.fq.slots[j] = (j < n) ? wfq_entry(cm1, c0, 1, 1, (u32)j) : wfq_entry(cm2, cm1, 1, 1, kWBotC);
         }
     }
+}
+
+// G-WFQ-YMC cells: every <value, dequeue reference> pair = <BOT, BOT>, one
+// 16-byte store per cell, grid-stride.
+__global__ void k_reset_cells(unsigned long long* pairs, u64 cells) {
+    ulonglong2* p = reinterpret_cast<ulonglong2*>(pairs);
+    const ulonglong2 e = make_ulonglong2(kVBot, kRefBot);
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < cells; j += stride) p[j] = e;
 }
 
 // ---------------------------------------------------------------------------
@@ -321,9 +333,12 @@ extern "C" int gq_reset(gq_handle h, void* stream) {
     const uint64_t base = h->start_ticket + 2 * d.capacity;
     if (d.kind == GQ_YMC) {
         const uint64_t cells = d.capacity + 1;
-        if (cudaMemsetAsync(d.cell_val, 0xFF, cells * 8, st) != cudaSuccess) return GQ_ERR_CUDA;
+        // eight 256-thread blocks per SM: one resident wave of the fill
+        const uint64_t sms = h->sm_count > 0 ? (uint64_t)h->sm_count : 1;
+        const uint64_t blocks = std::min<uint64_t>((cells + 255) / 256, 8 * sms);
+        k_reset_cells<<<(uint32_t)blocks, 256, 0, st>>>(d.cell_val, cells);
+        if (cudaGetLastError() != cudaSuccess) return GQ_ERR_CUDA;
         if (cudaMemsetAsync(d.cell_enq, 0, cells * 8, st) != cudaSuccess) return GQ_ERR_CUDA;
-        if (cudaMemsetAsync(d.cell_deq, 0, cells * 8, st) != cudaSuccess) return GQ_ERR_CUDA;
         if (cudaMemsetAsync(d.ymc_rec, 0, (uint64_t)d.max_threads * kYmcRecBytes, st) != cudaSuccess)
             return GQ_ERR_CUDA;
     } else {

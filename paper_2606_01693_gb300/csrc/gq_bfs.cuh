@@ -29,9 +29,9 @@ __device__ inline void ymc_cluster_clear(const gq_dev& q, u32 ct, u32 nct, cg::c
     const u64 used = max(ld_acq(q.ymc_tail), ld_acq(q.ymc_head)) + 65536;
     const u64 hi = used < q.capacity ? used : q.capacity;
     for (u64 i = 1 + ct; i <= hi; i += nct) {
-        q.cell_val[i] = ~0ull;
+        q.cell_val[2 * i] = ~0ull;    // <value, dequeue reference> pair
+        q.cell_deq[2 * i] = 0;
         q.cell_enq[i] = 0;
-        q.cell_deq[i] = 0;
     }
     cluster.sync();
     if (ct == 0) {

@@ -95,11 +95,18 @@ __device__ __forceinline__ void ymc_advance(u64* C, u64 v) {
 
 enum { kYValue = 0, kYUnusable = 1, kYEmpty = 2 };
 
+// Cell i's value and dequeue reference sit side by side in one 16-byte pair
+// (cell_val[2i], cell_deq[2i] = cell_val[2i + 1]): the dequeue that reads the
+// value and then claims the cell touches one L2 sector, already brought in by
+// the enqueue's CAS, instead of a second line in a second array.
+__device__ __forceinline__ u64* yval(const gq_dev& q, u64 i) { return q.cell_val + 2 * i; }
+__device__ __forceinline__ u64* ydeq(const gq_dev& q, u64 i) { return q.cell_deq + 2 * i; }
+
 // help_enq: settles cell i for the dequeuer `me` and returns kYValue with *v,
 // kYUnusable (try another cell), or kYEmpty (T <= i: no enqueue reached i).
 template <bool CNT = false>
 static __device__ __noinline__ int ymc_help_enq(const gq_dev& q, u32 me, u64 i, u64* v) {
-    u64* cv = q.cell_val + i;
+    u64* cv = yval(q, i);
     u64* ce = q.cell_enq + i;
     u64 x = ld_acq(cv);
     oc_add<CNT>(kOcLoad);
@@ -197,7 +204,7 @@ static __device__ __noinline__ int ymc_enq_slow(const gq_dev& q, u32 me, u64 v, 
             break;
         }
         u64 b = kRefBot;
-        if (cas(q.cell_enq + i, b, ytag(id, me)) && ld_acq(q.cell_val + i) != kVTop) {
+        if (cas(q.cell_enq + i, b, ytag(id, me)) && ld_acq(yval(q, i)) != kVTop) {
             u64 cur = id;
             cas(er + kYErId, cur, (u64)(-(i64)i));   // claim cell i (a helper may have claimed another)
             break;
@@ -210,7 +217,7 @@ static __device__ __noinline__ int ymc_enq_slow(const gq_dev& q, u32 me, u64 v, 
     }
     const u64 c = (u64)(-done);
     ymc_advance(q.ymc_tail, c);
-    st_rel(q.cell_val + c, v);
+    st_rel(yval(q, c), v);
     if (tk) *tk = c;
     return GQ_OK;
 }
@@ -230,7 +237,7 @@ static __device__ __noinline__ void ymc_help_deq(const gq_dev& q, u32 me, u32 p)
             if (!ycell_ok(q, (u64)i)) return;
             u64 v;
             const int s = ymc_help_enq(q, me, (u64)i, &v);
-            if (s == kYEmpty || (s == kYValue && ld_acq(q.cell_deq + i) == kRefBot)) cand = i;
+            if (s == kYEmpty || (s == kYValue && ld_acq(ydeq(q, i)) == kRefBot)) cand = i;
             else idx = ld_i(dr + kYDrIdx);
         }
         if (jt == kYScanLimit) break;   // never claim the request's own first cell unannounced
@@ -242,7 +249,7 @@ static __device__ __noinline__ void ymc_help_deq(const gq_dev& q, u32 me, u32 p)
         }
         if (idx < 0 || ld_i(dr + kYDrId) != id) return;    // completed
         u64 b = kRefBot;
-        if (ld_acq(q.cell_val + idx) == kVTop || cas(q.cell_deq + idx, b, (u64)p + 2) || b == (u64)p + 2) {
+        if (ld_acq(yval(q, idx)) == kVTop || cas(ydeq(q, idx), b, (u64)p + 2) || b == (u64)p + 2) {
             u64 cur = (u64)idx;
             cas(dr + kYDrIdx, cur, (u64)(-idx));
             return;
@@ -269,7 +276,7 @@ __device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
         const u64 i = warp_faa<MATCH, CNT>(q.ymc_tail, 1, q.batch_width);
         if (!ycell_ok(q, i)) return GQ_ERR_POOL_EXHAUSTED;
         u64 b = kVBot;
-        const bool ok = aref<u64>(q.cell_val[i]).compare_exchange_strong(b, x, kRel, kRlx);
+        const bool ok = aref<u64>(*yval(q, i)).compare_exchange_strong(b, x, kRel, kRlx);
         oc_cas<CNT>(ok);
         if (ok) {
             if (tk) *tk = i;
@@ -298,7 +305,7 @@ __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid, u64* tk = nullptr) 
         res = ymc_help_enq<CNT>(q, tid, i, &v);
         if (res == kYValue) {
             u64 b = kRefBot;
-            const bool ok = cas(q.cell_deq + i, b, kRefTop);
+            const bool ok = cas(ydeq(q, i), b, kRefTop);
             oc_cas<CNT>(ok);
             if (!ok) res = kYUnusable;   // a slow dequeue took it
         }
@@ -320,7 +327,7 @@ __device__ int ymc_dequeue(const gq_dev& q, T* out, u32 tid, u64* tk = nullptr) 
         }
         const u64 c = (u64)(-idx);
         ymc_advance(q.ymc_head, c);
-        v = ld_acq(q.cell_val + c);
+        v = ld_acq(yval(q, c));
         res = (v == kVTop) ? kYEmpty : kYValue;
         id = c;
     }
