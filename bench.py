@@ -40,12 +40,12 @@ CAPACITY = 1 << 20
 # DRAM bytes (read + write) per launch of each run kernel at the headline size.  G-WFQ-YMC: one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one kernel, one launch) of the
 # 2^18-thread case of the same workload, `bench.py --threads 262144 --steps 1 --warmup 1
-# --no-sweep --no-e2e --no-cpu --no-apps --no-batched --no-serving --kinds ymc`: 240724224 +
-# 157876992 bytes for 26.2 M operations (each ticket's cell touched once), scaled by the 4x
+# --no-sweep --no-e2e --no-cpu --no-apps --no-batched --no-serving --kinds ymc`: 240192768 +
+# 156758528 bytes for 26.2 M operations (each ticket's cell touched once), scaled by the 4x
 # operations of the headline launch (profiles/traffic_k_run_mixed_2p18.md).  The ring queues'
 # traffic is their workspace read once and does not scale with the operations, so it is not
 # extrapolated here.  Set an entry to None whenever that kernel changes.
-NCU_TRAFFIC = {"lfq": None, "wfq": None, "ymc": 4 * (240724224 + 157876992)}
+NCU_TRAFFIC = {"lfq": None, "wfq": None, "ymc": 4 * (240192768 + 156758528)}
 
 
 def parse():
