@@ -350,7 +350,9 @@ def bench_serving(gq, synth, kinds, dev, pool_graphs=1000, seed=2026):
     seed, i.e. log-uniform vertex counts), requests (graph, source) with Poisson
     arrivals at 100..10,000 req/s, admission against a 32 GiB budget.  Persistent
     device scheduler (clusters of 8 blocks fed by the mapped request ring) vs one
-    gq_bfs launch per request vs the adaptive mode that switches between the two.
+    gq_bfs launch per request vs the adaptive mode that switches between the two;
+    the persistent scheduler with its default gangs (up to 16 clusters for a
+    request on a graph of at least 2^17 vertices) and without (`_solo`).
     Latency = host-observed completion - arrival."""
     import torch
     scales = synth.rmat_pool_scales(pool_graphs, 10, 20, seed)
@@ -366,15 +368,17 @@ def bench_serving(gq, synth, kinds, dev, pool_graphs=1000, seed=2026):
         nreq = int(min(2000, max(200, rate)))
         gid, src, arr = synth.serving_requests(offs, nreq, float(rate), seed + rate)
         for k in kinds:
-            for mode in ("persistent", "per_request", "adaptive"):
-                r = gq.gq_serve(k, devg, gid, src, arr, mode=mode, cluster_blocks=8, budget_bytes=32 << 30)
+            for mode in ("persistent", "persistent_solo", "per_request", "adaptive"):
+                # persistent_solo: the scheduler without gangs (one cluster per request)
+                r = gq.gq_serve(k, devg, gid, src, arr, mode=mode.replace("_solo", ""), cluster_blocks=8,
+                                budget_bytes=32 << 30, gang_clusters=1 if mode.endswith("_solo") else 0)
                 lat = r["latency_s"] * 1e3
                 out["%s_%s_%d" % (k, mode, rate)] = {
                     "requests": nreq, "p50_ms": round(float(np.percentile(lat, 50)), 3),
                     "p99_ms": round(float(np.percentile(lat, 99)), 3),
                     "throughput_rps": round(nreq / r["wall_s"], 1), "admission_waits": int(r["admission_waits"]),
                     "peak_state_gib": round(r["peak_state_bytes"] / 2**30, 3), "slots": int(r["slots_used"]),
-                    "persistent_requests": int(r["persistent_requests"])}
+                    "persistent_requests": int(r["persistent_requests"]), "gang_requests": int(r["gang_requests"])}
     return out
 
 

@@ -23,6 +23,14 @@
  *                         the same stream) and takes the following requests;
  *                         after 0.5 ms with nothing to do it is stopped and
  *                         per-request launches resume.
+ * Gangs (persistent scheduler, gang_clusters > 1): a cluster takes a ticket
+ * only once the host has published it, so idle clusters hold none.  The
+ * cluster that takes a request on a large graph offers a gang (one at a time
+ * on the GPU); clusters with nothing published to take join it for up to
+ * 20 us, and the gang runs the request's BFS on the taker's queues with a
+ * barrier of its own between levels (thread 0 of each cluster meets the others
+ * on a device counter, bounded wait).  Requests on small graphs, or taken
+ * while another gang is forming, run on one cluster.
  * Admission (both modes, first come first served): a request is published or
  * launched only when its device state fits in the budget; it waits on the host
  * otherwise.  A request's state is counted as its graph's CSR (8 (n + 1) +
@@ -70,7 +78,12 @@ typedef struct {
                                     /* most budget_bytes                                      */
     uint32_t switch_backlog;        /* adaptive: pending launches that start the scheduler;   */
                                     /* 0 = 8                                                   */
-    uint32_t reserved;
+    uint32_t gang_clusters;         /* persistent / adaptive: most clusters that serve one     */
+                                    /* request together (a gang; at most 64, and at most the  */
+                                    /* slots); 1 = one cluster per request; 0 = default 16     */
+    uint32_t gang_min_vertices;     /* requests on graphs of at least this many vertices form  */
+                                    /* gangs; 0 = default 2^17                                 */
+    uint32_t reserved;              /* must be 0                                               */
 } gq_serve_config;
 
 typedef struct {
@@ -82,6 +95,8 @@ typedef struct {
     uint64_t persistent_requests;   /* requests the persistent scheduler served                */
     uint32_t slots_used;            /* clusters of the persistent scheduler (0: not used)      */
     int32_t status;                 /* GQ_OK or the first error                                */
+    uint64_t gang_requests;         /* requests the persistent scheduler served with a gang    */
+                                    /* of two or more clusters                                 */
 } gq_serve_result;
 
 /* Serves every request and returns when all are done (synchronous; uses the

@@ -546,19 +546,20 @@ class gq_serve_config(ctypes.Structure):
                 ("wait_limit_s", ctypes.c_double), ("ngraphs", ctypes.c_uint32), ("nrequests", ctypes.c_uint32),
                 ("graphs", ctypes.c_void_p), ("req_graph", ctypes.c_void_p), ("req_src", ctypes.c_void_p),
                 ("req_arrival_s", ctypes.c_void_p), ("req_out", ctypes.c_void_p),
-                ("switch_backlog", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("switch_backlog", ctypes.c_uint32), ("gang_clusters", ctypes.c_uint32),
+                ("gang_min_vertices", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class gq_serve_result(ctypes.Structure):
     _fields_ = [("latency_s", ctypes.c_void_p), ("wall_s", ctypes.c_double), ("peak_state_bytes", ctypes.c_uint64),
                 ("admission_waits", ctypes.c_uint64), ("edges_scanned", ctypes.c_uint64),
                 ("persistent_requests", ctypes.c_uint64), ("slots_used", ctypes.c_uint32),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("gang_requests", ctypes.c_uint64)]
 
 
 def gq_serve(kind, graphs, req_graph, req_src, arrival_s, mode="persistent", slots: int = 0,
              cluster_blocks: int = 4, budget_bytes: int = 32 << 30, outs=None, wait_limit_s: float = 0.0,
-             switch_backlog: int = 0) -> dict:
+             switch_backlog: int = 0, gang_clusters: int = 0, gang_min_vertices: int = 0) -> dict:
     """Serves BFS requests (include/gq_serve.h).
 
     graphs: list of (d_offsets int64, d_adj int32) device tensors (CSR).
@@ -585,9 +586,11 @@ def gq_serve(kind, graphs, req_graph, req_src, arrival_s, mode="persistent", slo
     lat = np.full(n, -1.0)
     cfg = gq_serve_config(kind, mode, slots, cluster_blocks, budget_bytes, wait_limit_s, len(graphs), n,
                           ctypes.cast(g, ctypes.c_void_p), rg.ctypes.data, rs.ctypes.data, ra.ctypes.data,
-                          None if out_arr is None else ctypes.cast(out_arr, ctypes.c_void_p), switch_backlog, 0)
-    res = gq_serve_result(lat.ctypes.data, 0.0, 0, 0, 0, 0, 0, 0)
+                          None if out_arr is None else ctypes.cast(out_arr, ctypes.c_void_p), switch_backlog,
+                          gang_clusters, gang_min_vertices, 0)
+    res = gq_serve_result(lat.ctypes.data, 0.0, 0, 0, 0, 0, 0, 0, 0)
     _check(lib.gq_serve(ctypes.byref(cfg), ctypes.byref(res)), "gq_serve")
     return {"latency_s": lat, "wall_s": res.wall_s, "peak_state_bytes": res.peak_state_bytes,
             "admission_waits": res.admission_waits, "edges_scanned": res.edges_scanned,
-            "persistent_requests": res.persistent_requests, "slots_used": res.slots_used}
+            "persistent_requests": res.persistent_requests, "slots_used": res.slots_used,
+            "gang_requests": res.gang_requests}

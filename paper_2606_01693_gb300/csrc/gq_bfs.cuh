@@ -22,8 +22,22 @@ __device__ __forceinline__ void bfs_visit(const gq_dev& nxt, u32* dist, u32 w, u
     if (queue_enqueue<unsigned int, KIND>(nxt, w, tid) == GQ_OK) ++*cnt;
 }
 
+// Barrier of the threads that run one BFS instance when they form one
+// thread-block cluster: the hardware cluster barrier (release / acquire at
+// cluster scope).  A barrier object returns false when the group has to give
+// the instance up (only a multi-cluster barrier whose bounded wait expired
+// does); every thread of the group gets the same answer.
+struct ClusterSync {
+    cg::cluster_group& cluster;
+    __device__ bool operator()() const {
+        cluster.sync();
+        return true;
+    }
+};
+
 // Clears the cells an instance used and rewinds T and H (G-WFQ-YMC never reuses cells).
-__device__ inline void ymc_cluster_clear(const gq_dev& q, u32 ct, u32 nct, cg::cluster_group& cluster) {
+template <class Sync>
+__device__ inline bool ymc_group_clear(const gq_dev& q, u32 ct, u32 nct, const Sync& sync) {
     // cells up to max(T, H), plus a margin for cells a slow-dequeue helper may
     // have scanned past the completing candidate
     const u64 used = max(ld_acq(q.ymc_tail), ld_acq(q.ymc_head)) + 65536;
@@ -33,11 +47,12 @@ __device__ inline void ymc_cluster_clear(const gq_dev& q, u32 ct, u32 nct, cg::c
         q.cell_deq[2 * i] = 0;
         q.cell_enq[i] = 0;
     }
-    cluster.sync();
+    if (!sync()) return false;
     if (ct == 0) {
         st_rel(q.ymc_tail, 1);
         st_rel(q.ymc_head, 1);
     }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -318,17 +333,20 @@ __device__ bool level_chunks(const gq_dev& nxt, const LevelCtx& c, u32* cnt, u64
     }
 }
 
-// One level-synchronous BFS by the threads of a thread-block cluster on the
-// frontier queues qa / qb (left empty).  ctl[0..2]: rotating frontier counts;
-// table: this cluster's chunk map of `cap` positions.  Returns the number of
-// levels; adds scanned edges to *edges; a chunk wait that expired is latched
-// in *err (nullable) as 1.  That is the only failure of the chunk phase: a
-// vertex whose chunks do not fit in the map is scanned by the gather instead
-// (chunk_publish), so a full map is not an error.
-template <int KIND>
-__device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* table, u64 cap,
-                           const gq_bfs_instance& g, u32* dist, u32 ct, u32 nct, cg::cluster_group& cluster,
-                           u64* edges, unsigned long long* err) {
+constexpr u32 kBfsAborted = 0xFFFFFFFFu;
+
+// One level-synchronous BFS by a group of nct threads (thread ct of the group;
+// `sync` is the group's barrier) on the frontier queues qa / qb (left empty).
+// ctl[0..2]: rotating frontier counts; table: the group's chunk map of `cap`
+// positions.  Returns the number of levels, or kBfsAborted when a barrier gave
+// up (the distances are then incomplete); adds scanned edges to *edges; a chunk
+// wait that expired is latched in *err (nullable) as 1.  That is the only
+// failure of the chunk phase: a vertex whose chunks do not fit in the map is
+// scanned by the gather instead (chunk_publish), so a full map is not an error.
+template <int KIND, class Sync>
+__device__ u32 group_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* table, u64 cap,
+                         const gq_bfs_instance& g, u32* dist, u32 ct, u32 nct, const Sync& sync,
+                         u64* edges, unsigned long long* err) {
     const u32 cw = ct >> 5, nwarps = nct >> 5;
     const u64* off = reinterpret_cast<const u64*>(g.d_offsets);
     u64 maxdeg = 0;
@@ -348,12 +366,12 @@ __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* ta
         st_rlx(ctl + 2, 0);
         chunk_reset_all(table);
     }
-    cluster.sync();
+    if (!sync()) return kBfsAborted;
     if (ct == 0) {
         dist[g.src] = 0;
         if (queue_enqueue<unsigned int, KIND>(qa, g.src, 0) == GQ_OK) st_rlx(ctl + 0, 1);
     }
-    cluster.sync();
+    if (!sync()) return kBfsAborted;
     // without a vertex of degree >= kHeavyDeg no chunk is ever published
     const bool chunks = ld_acq(table + kTabMaxDeg) >= kHeavyDeg;
     u32 level = 0;
@@ -375,15 +393,22 @@ __device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* ta
         if (chunks && !level_chunks<KIND>(nxt, c, &cnt, edges) && (threadIdx.x & 31) == 0 && err)
             atomicCAS(err, 0ull, 1ull);
         warp_add_full(reinterpret_cast<unsigned long long*>(ctl + (level + 1) % 3), cnt);
-        cluster.sync();
+        if (!sync()) return kBfsAborted;
     }
     if (KIND == GQ_YMC) {
-        ymc_cluster_clear(qa, ct, nct, cluster);
-        ymc_cluster_clear(qb, ct, nct, cluster);
+        if (!ymc_group_clear(qa, ct, nct, sync) || !ymc_group_clear(qb, ct, nct, sync)) return kBfsAborted;
     }
-    cluster.sync();
+    if (!sync()) return kBfsAborted;
     if (ct == 0) st_rlx(table + kTabMaxDeg, 0);      // every thread read it before the last barrier
     return level;
+}
+
+// The group is one thread-block cluster.
+template <int KIND>
+__device__ u32 cluster_bfs(const gq_dev& qa, const gq_dev& qb, u64* ctl, u64* table, u64 cap,
+                           const gq_bfs_instance& g, u32* dist, u32 ct, u32 nct, cg::cluster_group& cluster,
+                           u64* edges, unsigned long long* err) {
+    return group_bfs<KIND>(qa, qb, ctl, table, cap, g, dist, ct, nct, ClusterSync{cluster}, edges, err);
 }
 
 }  // namespace gqd

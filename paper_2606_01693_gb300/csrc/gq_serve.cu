@@ -59,6 +59,25 @@ struct ServeShared {
 };
 
 constexpr u64 kNoTicket = ~0ull;
+constexpr u64 kMember = ~0ull - 1;      // ctl[0]: the cluster joined another cluster's gang
+constexpr u64 kSealed = 1ull << 63;     // gang join word: closed
+constexpr u64 kGangWaitNs = 20000;      // a gang leader waits this long for idle clusters to join
+// Chunk-map positions of one slot's search: 2^18 chunks of 128 edges cover the
+// heavy vertices of any level of the pool's largest graphs (scale 20: about
+// 3.3 * 10^7 directed edges), so no hub falls back to one warp's gather, which
+// a gang's extra warps could not share.
+constexpr u64 kServeChunkCap = 1u << 18;
+
+// Gang record of a slot (8 words in device memory).  A gang is one request
+// served by several clusters: the cluster that took the ticket (the leader)
+// offers the gang, idle clusters join, and all of them run one BFS on the
+// leader's queues with a barrier of their own between levels.
+enum {
+    kGJoin = 0,     // <epoch 31 | joined count 32>, kSealed once the leader closed the gang
+    kGGo = 1,       // <epoch | member count> once closed (members wait for it)
+    kGBarCnt = 2,   // barrier arrivals of the current phase
+    kGBarGen = 3    // barrier generation
+};
 
 struct ServeK {
     ServeEntry* ring;            // device view of the mapped ring
@@ -69,8 +88,13 @@ struct ServeK {
     u64* claim;                  // next ticket (device memory)
     u64* ctl;                    // 8 words per slot (device memory)
     u64* tables;                 // chunk map per slot (device memory)
-    unsigned long long* stats;   // edges scanned, requests served, first error (1 = wait limit, 2 = bad request)
+    unsigned long long* stats;   // edges scanned, requests served, first error (1 = wait limit, 2 = bad
+                                 // request), requests served by gangs
     u64 wait_ns;
+    u64* gang;                   // 8 words per slot (device memory)
+    u64* gang_open;              // <epoch | leader slot + 1> of the gang open for joining, 0 = none
+    u32 gang_max;                // most clusters per request (1 = no gangs)
+    u32 gang_min_n;              // requests on graphs of at least this many vertices form gangs
 };
 
 using sys_ref = cuda::atomic_ref<u64, cuda::thread_scope_system>;
@@ -80,70 +104,202 @@ __device__ __forceinline__ u64 ld_rlx_sys(u64* p) { return sys_ref(*p).load(kRlx
 __device__ __forceinline__ void st_rel_sys(u64* p, u64 v) { sys_ref(*p).store(v, kRel); }
 __device__ __forceinline__ void st_rlx_sys(u64* p, u64 v) { sys_ref(*p).store(v, kRlx); }
 
-// Thread 0 of a cluster: the next ticket whose entry the host has published,
-// with its fields copied into ctl[4..5]; kNoTicket when there is none left,
-// the host asked to stop, or the wait limit expired (error latched).
-__device__ u64 claim_request(const ServeK& a, u64* ctl) {
-    const u64 t = faa_rlx(a.claim, 1);
-    if (t >= a.nreq) return kNoTicket;
-    ServeEntry* e = a.ring + (t & a.ring_mask);
-    const u64 t0 = globaltimer();
-    for (u32 polls = 0;; ++polls) {
-        if (ld_acq_sys(&e->seq) == t + 1) break;
-        if (ld_rlx_sys(&a.sh->stop)) return kNoTicket;
-        if (globaltimer() - t0 > a.wait_ns) {
-            atomicCAS(a.stats + 2, 0ull, 1ull);
-            return kNoTicket;
-        }
-        __nanosleep(polls < 256 ? 64 : 256);
-    }
+// Thread 0 of a cluster that took ticket t (entry e): checks the request,
+// copies its fields into ctl[4..5] and, for a large graph, forms a gang.
+// ctl[0] = t, ctl[7] = <members 16 | rank 24 | leader slot 24> (rank 0, leader
+// = own slot); ctl[0] = kNoTicket for a bad request (the cluster leaves).
+__device__ void take_request(const ServeK& a, u32 slot, u64* ctl, u64 t, ServeEntry* e) {
     const u64 req = ld_rlx_sys(&e->req);
     const u32 g = (u32)req, s = (u32)(req >> 32);
     if (g >= a.ngraphs || s >= a.graphs[g].n) {
         atomicCAS(a.stats + 2, 0ull, 2ull);
         st_rlx_sys(&e->levels, ~0ull);
         st_rel_sys(&e->done, t + 1);
-        return kNoTicket;
+        st_rlx(ctl, kNoTicket);
+        return;
     }
     st_rlx(ctl + 4, ((u64)s << 32) | g);
     st_rlx(ctl + 5, ld_rlx_sys(&e->dist));
-    return t;
+    u64 members = 1;
+    if (a.gang_max > 1 && a.graphs[g].n >= a.gang_min_n) {
+        u64* gr = a.gang + 8 * (u64)slot;
+        const u64 ep = ((t + 1) & 0x7FFFFFFFull) | ((t + 1) & 0x7FFFFFFFull ? 0 : 1);
+        st_rlx(gr + kGGo, 0);
+        st_rlx(gr + kGBarCnt, 0);
+        st_rel(gr + kGJoin, ep << 32);
+        const u64 offer = (ep << 32) | (slot + 1);
+        if (atomicCAS(reinterpret_cast<unsigned long long*>(a.gang_open), 0ull, offer) == 0ull) {
+            // wait (boundedly) for idle clusters, then close the gang
+            const u64 t0 = globaltimer();
+            while ((u32)ld_acq(gr + kGJoin) + 1 < a.gang_max && globaltimer() - t0 < kGangWaitNs) __nanosleep(64);
+            atomicCAS(reinterpret_cast<unsigned long long*>(a.gang_open), offer, 0ull);
+            const u64 j = atomicOr(reinterpret_cast<unsigned long long*>(gr + kGJoin), kSealed);
+            members = 1 + (u32)j;
+        }
+        // the member count (and, before it, ctl[4..5]) is released to the members
+        st_rel(gr + kGGo, (ep << 32) | members);
+    }
+    st_rlx(ctl + 7, (members << 48) | slot);
+    st_rlx(ctl, t);
 }
 
+// Thread 0 of an idle cluster: joins the open gang if there is one and it has
+// room.  On success ctl[0] = kMember and ctl[7] describes the gang.
+__device__ bool try_join(const ServeK& a, u32 slot, u64* ctl) {
+    const u64 o = ld_acq(a.gang_open);
+    if (o == 0) return false;
+    const u32 lead = (u32)o - 1;
+    const u64 ep = o >> 32;
+    if (lead == slot) return false;
+    u64* gr = a.gang + 8 * (u64)lead;
+    u64 j = ld_acq(gr + kGJoin);
+    u32 rank = 0;
+    for (u32 it = 0; it < 64 && rank == 0; ++it) {
+        if ((j >> 32) != ep || (u32)j + 1 >= a.gang_max) return false;   // another gang, closed, or full
+        const u64 w = atomicCAS(reinterpret_cast<unsigned long long*>(gr + kGJoin), j, j + 1);
+        if (w == j) rank = (u32)j + 1;
+        else j = w;
+    }
+    if (rank == 0) return false;
+    const u64 t0 = globaltimer();
+    u64 go = ld_acq(gr + kGGo);
+    for (u32 polls = 0; (go >> 32) != ep; ++polls) {
+        if (globaltimer() - t0 > a.wait_ns) {
+            atomicCAS(a.stats + 2, 0ull, 1ull);
+            st_rlx(ctl, kNoTicket);
+            return true;
+        }
+        __nanosleep(32);
+        go = ld_acq(gr + kGGo);
+    }
+    st_rlx(ctl + 7, ((go & 0xFFFFull) << 48) | ((u64)rank << 24) | lead);
+    st_rlx(ctl, kMember);
+    return true;
+}
+
+// Thread 0 of a cluster: the next piece of work, in ctl[0] (a ticket, kMember,
+// or kNoTicket when there is none left, the host asked to stop, or the wait
+// limit expired with no ticket published, error latched).  A ticket is taken
+// only once the host has published it (a CAS on the claim counter from the
+// ticket it read), so an idle cluster holds no ticket and can join a gang.
+__device__ void next_work(const ServeK& a, u32 slot, u64* ctl) {
+    u64 last = ~0ull, t0 = 0;
+    for (u32 polls = 0;; ++polls) {
+        const u64 c = ld_acq(a.claim);
+        if (c >= a.nreq) break;
+        ServeEntry* e = a.ring + (c & a.ring_mask);
+        if (ld_acq_sys(&e->seq) == c + 1) {
+            if (atomicCAS(reinterpret_cast<unsigned long long*>(a.claim), c, c + 1) == c) {
+                take_request(a, slot, ctl, c, e);
+                return;
+            }
+            continue;                       // another cluster took it: look at the next ticket
+        }
+        if (a.gang_max > 1 && try_join(a, slot, ctl)) return;
+        if (ld_rlx_sys(&a.sh->stop)) break;
+        if (c != last) {
+            last = c;
+            t0 = globaltimer();
+        } else if (globaltimer() - t0 > a.wait_ns) {
+            atomicCAS(a.stats + 2, 0ull, 1ull);
+            break;
+        }
+        __nanosleep(polls < 256 ? 64 : 256);
+    }
+    st_rlx(ctl, kNoTicket);
+}
+
+// Barrier of a gang: the cluster barrier, then thread 0 of each cluster meets
+// the others on the leader's counter (arrive with a fetch-add after a fence,
+// wait boundedly for the generation to move), then the cluster barrier again.
+// Returns false in every thread of the cluster once a wait expired (latched).
+struct GangSync {
+    cg::cluster_group& cluster;
+    u64* gr;                     // the leader's gang record
+    u64* flag;                   // this cluster's broadcast word
+    u32 members;
+    bool lead;                   // thread 0 of this cluster
+    u64 wait_ns;
+    unsigned long long* err;
+    __device__ bool operator()() const {
+        cluster.sync();
+        if (lead) {
+            bool ok = true;
+            const u64 g0 = ld_acq(gr + kGBarGen);
+            __threadfence();
+            if (atomicAdd(reinterpret_cast<unsigned long long*>(gr + kGBarCnt), 1ull) + 1 == members) {
+                st_rlx(gr + kGBarCnt, 0);
+                st_rel(gr + kGBarGen, g0 + 1);
+            } else {
+                const u64 t0 = globaltimer();
+                while (ld_acq(gr + kGBarGen) == g0) {
+                    if (globaltimer() - t0 > wait_ns) {
+                        atomicCAS(err, 0ull, 1ull);
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+            st_rlx(flag, ok ? 0 : 1);
+        }
+        cluster.sync();
+        return ld_rlx(flag) == 0;
+    }
+};
+
 template <int KIND>
-__global__ void __launch_bounds__(256) k_serve(const gq_dev* __restrict__ fq, const __grid_constant__ ServeK a) {
+__global__ void __launch_bounds__(256, 4) k_serve(const gq_dev* __restrict__ fq, const __grid_constant__ ServeK a) {
     cg::cluster_group cluster = cg::this_cluster();
     const u32 cblocks = cluster.num_blocks();
     const u32 slot = blockIdx.x / cblocks;
     const u32 ct = cluster.block_rank() * blockDim.x + threadIdx.x;
     const u32 nct = cblocks * blockDim.x;
-    u64* ctl = a.ctl + 8 * (u64)slot;     // [0] ticket, [1..3] frontier counts, [4] src|graph, [5] dist
-    const gq_dev& qa = fq[2 * slot];
-    const gq_dev& qb = fq[2 * slot + 1];
-    u64 edges = 0, served = 0;
-    for (u64 guard = 0; guard <= a.nreq; ++guard) {
-        if (ct == 0) st_rlx(ctl, claim_request(a, ctl));
+    // [0] ticket / kMember / kNoTicket, [1..3] frontier counts, [4] src|graph,
+    // [5] dist, [6] gang barrier flag, [7] gang <members | rank | leader>
+    u64* ctl = a.ctl + 8 * (u64)slot;
+    u64 edges = 0, served = 0, ganged = 0;
+    // every iteration takes a ticket or joins a gang that took one
+    for (u64 guard = 0; guard <= 2 * a.nreq; ++guard) {
+        if (ct == 0) next_work(a, slot, ctl);
         cluster.sync();
         const u64 t = ld_acq(ctl);
-        const u64 gs = ld_acq(ctl + 4);
-        u32* dist = reinterpret_cast<u32*>(ld_acq(ctl + 5));
-        cluster.sync();                      // every thread has read ctl before it is reused
+        const u64 gd = ld_acq(ctl + 7);
         if (t == kNoTicket) break;
+        const u32 lead = (u32)(gd & 0xFFFFFFull), rank = (u32)((gd >> 24) & 0xFFFFFFull);
+        const u32 members = (u32)(gd >> 48);
+        u64* lctl = a.ctl + 8 * (u64)lead;
+        const u64 gs = ld_acq(lctl + 4);
+        u32* dist = reinterpret_cast<u32*>(ld_acq(lctl + 5));
+        cluster.sync();                      // every thread has read ctl before it is reused
         gq_bfs_instance g = a.graphs[(u32)gs];
         g.src = (u32)(gs >> 32);
-        u64* table = a.tables + slot * (chunk_map_bytes(kClusterChunkCap) / 8);
-        const u32 levels = cluster_bfs<KIND>(qa, qb, ctl + 1, table, kClusterChunkCap, g, dist, ct, nct, cluster,
-                                             &edges, a.stats + 2);
-        if (ct == 0) {
+        u64* table = a.tables + lead * (chunk_map_bytes(kServeChunkCap) / 8);
+        const gq_dev& qa = fq[2 * lead];
+        const gq_dev& qb = fq[2 * lead + 1];
+        u32 levels;
+        if (members <= 1) {
+            levels = cluster_bfs<KIND>(qa, qb, lctl + 1, table, kServeChunkCap, g, dist, ct, nct, cluster, &edges,
+                                       a.stats + 2);
+        } else {
+            const GangSync sync{cluster, a.gang + 8 * (u64)lead, ctl + 6, members, ct == 0, a.wait_ns, a.stats + 2};
+            levels = group_bfs<KIND>(qa, qb, lctl + 1, table, kServeChunkCap, g, dist, rank * nct + ct,
+                                     members * nct, sync, &edges, a.stats + 2);
+        }
+        if (ct == 0 && t != kMember) {
             ServeEntry* e = a.ring + (t & a.ring_mask);
             __threadfence_system();
-            st_rlx_sys(&e->levels, levels);
+            st_rlx_sys(&e->levels, levels == kBfsAborted ? ~0ull : (u64)levels);
             st_rel_sys(&e->done, t + 1);
             ++served;
+            ganged += members > 1;
         }
+        if (levels == kBfsAborted) break;
     }
     warp_add_full(a.stats, edges);
     if (ct == 0 && served) atomicAdd(a.stats + 1, served);
+    if (ct == 0 && ganged) atomicAdd(a.stats + 3, ganged);
 }
 
 // ---------------------------------------------------------------------------
@@ -351,7 +507,10 @@ struct Persistent {
         slots = c.slots ? c.slots : (u32)fit;
         if (slots > (u32)fit) slots = (u32)fit;
         if ((u64)slots > c.nrequests) slots = c.nrequests;
-        int s = fr.create(2ull * slots, c.kind, queue_capacity(c.kind, nmax), cb * 256, st);
+        u32 gang = c.gang_clusters ? c.gang_clusters : 16;
+        if (gang > slots) gang = slots;
+        // a gang runs on its leader's queues: records for every thread of a gang
+        int s = fr.create(2ull * slots, c.kind, queue_capacity(c.kind, nmax), cb * 256 * gang, st);
         if (s != GQ_OK) return s;
 
         ring_n = 1;
@@ -369,10 +528,11 @@ struct Persistent {
         entry_req.assign(ring_n, 0);
         entry_busy.assign(ring_n, 0);
 
-        const u64 o_ctl = 256;
-        o_stats = round256(o_ctl + 64ull * slots);
+        const u64 o_ctl = 256;                       // claim counter at 0, open gang word at 128
+        const u64 o_gang = round256(o_ctl + 64ull * slots);
+        o_stats = round256(o_gang + 64ull * slots);
         const u64 o_tables = o_stats + 256,
-                  o_views = round256(o_tables + slots * chunk_map_bytes(kClusterChunkCap)),
+                  o_views = round256(o_tables + slots * chunk_map_bytes(kServeChunkCap)),
                   o_graphs = round256(o_views + 2ull * slots * sizeof(gq_dev)),
                   total = round256(o_graphs + (u64)c.ngraphs * sizeof(gq_bfs_instance));
         if (cudaMalloc(&dev, total) != cudaSuccess) {
@@ -401,6 +561,10 @@ struct Persistent {
         a.stats = reinterpret_cast<unsigned long long*>(d + o_stats);
         a.tables = reinterpret_cast<u64*>(d + o_tables);
         a.wait_ns = (u64)((c.wait_limit_s > 0 ? c.wait_limit_s : 30.0) * 1e9);
+        a.gang = reinterpret_cast<u64*>(d + o_gang);
+        a.gang_open = reinterpret_cast<u64*>(d + 128);
+        a.gang_max = gang;
+        a.gang_min_n = c.gang_min_vertices ? c.gang_min_vertices : (1u << 17);
         dv = reinterpret_cast<const gq_dev*>(d + o_views);
         return GQ_OK;
     }
@@ -412,7 +576,7 @@ struct Persistent {
             ring[e].done = 0;
         }
         __atomic_store_n(&sh->stop, 0ull, __ATOMIC_RELEASE);
-        if (cudaMemsetAsync(a.claim, 0, sizeof(u64), st) != cudaSuccess) return GQ_ERR_CUDA;
+        if (cudaMemsetAsync(a.claim, 0, 256, st) != cudaSuccess) return GQ_ERR_CUDA;   // claim, open gang
         a.nreq = limit;
         const cudaError_t e = c.kind == GQ_LFQ ? launch_serve<GQ_LFQ>(slots, c.cluster_blocks, dv, a, st)
                               : c.kind == GQ_WFQ ? launch_serve<GQ_WFQ>(slots, c.cluster_blocks, dv, a, st)
@@ -476,12 +640,13 @@ struct Persistent {
 
     // Device error word and edge count (after the last episode ended).
     int finish(gq_serve_result& r, cudaStream_t st) {
-        unsigned long long st3[3] = {0, 0, 0};
+        unsigned long long st3[4] = {0, 0, 0, 0};
         if (cudaStreamSynchronize(st) != cudaSuccess ||
             cudaMemcpy(st3, d + o_stats, sizeof(st3), cudaMemcpyDeviceToHost) != cudaSuccess)
             return GQ_ERR_CUDA;
         r.edges_scanned = st3[0];
         r.persistent_requests = st3[1];
+        r.gang_requests = st3[3];
         if (st3[2]) return st3[2] == 2 ? GQ_ERR_INVALID : GQ_ERR_TIMEOUT;
         return fr.status(st);
     }
@@ -660,6 +825,7 @@ int validate(const gq_serve_config* c, const gq_serve_result* r) {
     if (!c->ngraphs || !c->nrequests || !c->graphs || !c->req_graph || !c->req_src || !c->req_arrival_s)
         return GQ_ERR_INVALID;
     if (!(c->wait_limit_s >= 0) || c->budget_bytes == 0) return GQ_ERR_INVALID;
+    if (c->gang_clusters > 64 || c->reserved != 0) return GQ_ERR_INVALID;
     for (u32 g = 0; g < c->ngraphs; ++g) {
         const gq_bfs_instance& x = c->graphs[g];
         if (x.n == 0 || x.n >= 0xFFFFFFFFull || !x.d_offsets || !x.d_adj) return GQ_ERR_INVALID;
@@ -681,6 +847,7 @@ extern "C" int gq_serve(const gq_serve_config* cfg, gq_serve_result* res) {
     res->wall_s = 0;
     res->peak_state_bytes = res->admission_waits = res->edges_scanned = res->persistent_requests = 0;
     res->slots_used = 0;
+    res->gang_requests = 0;
     res->status = GQ_OK;
     for (u32 i = 0; i < c.nrequests; ++i) res->latency_s[i] = -1.0;
 

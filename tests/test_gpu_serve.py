@@ -136,6 +136,47 @@ def test_request_larger_than_budget_rejected(pool):
     assert ei.value.status == gq.GQ_ERR_INVALID
 
 
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("rate", [300.0, 6000.0])
+def test_gangs_match_cpu_bfs(pool, kind, rate):
+    """Gangs: every request asks for up to 4 clusters (gang_min_vertices 1).  At a low
+    rate idle clusters join and gangs form; at a high rate most requests run on one
+    cluster.  Distances equal the oracle's either way, and the edges scanned by all
+    members add up to the reached edges."""
+    host, dev = pool
+    gid, src, arr = synth.serving_requests([h[0] for h in host], 40, rate, seed=31)
+    outs = _outs(host, gid)
+    r = gq.gq_serve(kind, dev, gid, src, arr, mode="persistent", slots=8, cluster_blocks=2, outs=outs,
+                    gang_clusters=4, gang_min_vertices=1)
+    assert (r["latency_s"] >= 0).all()
+    want = _expected(host, gid, src)
+    for o, w in zip(outs, want):
+        assert (o.cpu().numpy().view(np.uint32) == w).all()
+    reached_edges = sum(int(np.diff(host[g][0].astype(np.int64))[w != 0xFFFFFFFF].sum()) for g, w in zip(gid, want))
+    assert r["edges_scanned"] == reached_edges
+    assert r["persistent_requests"] == len(gid)
+    if rate < 1000:
+        assert r["gang_requests"] > 0, r
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_gangs_on_large_graphs_only(kind):
+    """Only requests on graphs of at least gang_min_vertices vertices form gangs; a
+    scale-16 graph served by gangs of up to 8 eight-block clusters gives the oracle's
+    distances."""
+    host = [synth.rmat_csr_fast(8, seed=61), synth.rmat_csr_fast(16, seed=62)]
+    dev = [(torch.from_numpy(o.view(np.int64)).cuda(), torch.from_numpy(a.view(np.int32)).cuda()) for o, a in host]
+    gid = np.array([0, 1, 0, 1, 0, 1], dtype=np.uint32)
+    src = np.array([0, 0, 5, 17, 9, 3], dtype=np.uint32)
+    arr = np.arange(6) * 2e-3
+    outs = _outs(host, gid)
+    r = gq.gq_serve(kind, dev, gid, src, arr, mode="persistent", slots=16, cluster_blocks=8, outs=outs,
+                    gang_clusters=8, gang_min_vertices=1 << 12)
+    for i, o in enumerate(outs):
+        assert (o.cpu().numpy().view(np.uint32) == oracle.bfs(host[gid[i]][0], host[gid[i]][1], int(src[i]))).all(), i
+    assert 0 < r["gang_requests"] <= 3, r
+
+
 def test_ring_wraps(pool):
     """More requests than ring entries (4096): entries are reused once their request is done."""
     host, dev = pool

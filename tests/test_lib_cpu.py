@@ -110,7 +110,8 @@ def _serve_cfg(**kw):
                              cluster_blocks=kw.pop("cluster_blocks", 2), budget_bytes=kw.pop("budget", 1 << 30),
                              wait_limit_s=kw.pop("wait", 0.0), ngraphs=kw.pop("ngraphs", 2), nrequests=len(rg),
                              graphs=ctypes.cast(g, ctypes.c_void_p).value, req_graph=rg.ctypes.data,
-                             req_src=rs.ctypes.data, req_arrival_s=ra.ctypes.data, req_out=None)
+                             req_src=rs.ctypes.data, req_arrival_s=ra.ctypes.data, req_out=None,
+                             gang_clusters=kw.pop("gang", 0), reserved=kw.pop("reserved", 0))
     lat = np.zeros(len(rg))
     res = gq.gq_serve_result(latency_s=lat.ctypes.data)
     keep.append(lat)
@@ -120,7 +121,7 @@ def _serve_cfg(**kw):
 @pytest.mark.parametrize("change", [
     {"kind": 7}, {"mode": 3}, {"cluster_blocks": 3}, {"cluster_blocks": 32}, {"req_graph": [0, 2, 0]}, {"req_src": [3, 50, 99]},
     {"arrival": [0.0, 0.2, 0.1]}, {"arrival": [0.0, float("nan"), 0.2]}, {"budget": 0}, {"wait": -1.0},
-    {"ngraphs": 0},
+    {"ngraphs": 0}, {"gang": 65}, {"reserved": 1},
 ])
 def test_serve_rejects_bad_config(change):
     cfg, res, keep = _serve_cfg(**change)
