@@ -36,7 +36,9 @@
  * otherwise.  A request's state is counted as its graph's CSR (8 (n + 1) +
  * 4 m bytes), its distance array (4 n bytes) and two frontier queues of its own
  * size (gq_workspace_bytes of the kind at capacity max(n, 4096) rounded up to
- * a power of two; G-WFQ-YMC: 4 n + 2^18 cells).
+ * a power of two; G-WFQ-YMC: 4 n + 2^18 cells), with per-thread records for
+ * the threads that may run it: a cluster, a gang of clusters for a graph that
+ * forms gangs, one gq_bfs grid per request; adaptive mode counts the larger.
  * Latency = the time the host sees the request done minus its arrival time.
  * A request's distances do not depend on what else is being served: BFS hop
  * counts are unique, whatever the claim order.

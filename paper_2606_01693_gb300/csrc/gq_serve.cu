@@ -62,10 +62,13 @@ constexpr u64 kNoTicket = ~0ull;
 constexpr u64 kMember = ~0ull - 1;      // ctl[0]: the cluster joined another cluster's gang
 constexpr u64 kSealed = 1ull << 63;     // gang join word: closed
 constexpr u64 kGangWaitNs = 20000;      // a gang leader waits this long for idle clusters to join
-// Chunk-map positions of one slot's search: 2^18 chunks of 128 edges cover the
-// heavy vertices of any level of the pool's largest graphs (scale 20: about
-// 3.3 * 10^7 directed edges), so no hub falls back to one warp's gather, which
-// a gang's extra warps could not share.
+// Chunk-map positions of one slot's table.  A gang uses all 2^18 (chunks of 128
+// edges for the heavy vertices of any level of the pool's largest graphs,
+// scale 20: about 3.3 * 10^7 directed edges), so no hub falls back to one
+// warp's gather, which the gang's other warps could not share (with 2^14 a
+// 12-cluster gang took 17-22 ms on a scale-20 graph instead of 1 ms).  One
+// cluster alone keeps the cluster search's 2^14 (one scale-20 search: 16 ms
+// with it, 21 ms with the full map, G-WFQ-YMC).
 constexpr u64 kServeChunkCap = 1u << 18;
 
 // Gang record of a slot (8 words in device memory).  A gang is one request
@@ -209,11 +212,15 @@ __device__ void next_work(const ServeK& a, u32 slot, u64* ctl) {
     st_rlx(ctl, kNoTicket);
 }
 
-// Barrier of a gang: the cluster barrier, then thread 0 of each cluster meets
+// Barrier of the clusters that serve one request.  One cluster: the cluster
+// barrier.  A gang: the cluster barrier, then thread 0 of each cluster meets
 // the others on the leader's counter (arrive with a fetch-add after a fence,
 // wait boundedly for the generation to move), then the cluster barrier again.
 // Returns false in every thread of the cluster once a wait expired (latched).
-struct GangSync {
+// The gang part is a call out of line, so that one search body (the
+// one-cluster search with a call in its barrier) is inlined into the scheduler
+// kernel, not one per barrier type.
+struct ServeSync {
     cg::cluster_group& cluster;
     u64* gr;                     // the leader's gang record
     u64* flag;                   // this cluster's broadcast word
@@ -222,6 +229,14 @@ struct GangSync {
     u64 wait_ns;
     unsigned long long* err;
     __device__ bool operator()() const {
+        if (members <= 1) {
+            cluster.sync();
+            return true;
+        }
+        return gang_sync(cluster, gr, flag, members, lead, wait_ns, err);
+    }
+    static __device__ __noinline__ bool gang_sync(cg::cluster_group& cluster, u64* gr, u64* flag, u32 members,
+                                                  bool lead, u64 wait_ns, unsigned long long* err) {
         cluster.sync();
         if (lead) {
             bool ok = true;
@@ -249,8 +264,13 @@ struct GangSync {
     }
 };
 
+// Registers: G-LFQ's and G-WFQ-YMC's kernels are held to 64 (four 256-thread
+// blocks per SM: 74 eight-block clusters on the GPU; unbounded, the compiler
+// takes 115 and 80, and 36 and 51 clusters fit).  G-WFQ's takes 64 unbounded,
+// and bounding it anyway cost it 30 % of its requests per second at
+// saturation (3.2 against 4.6 k req/s at 10,000 req/s offered).
 template <int KIND>
-__global__ void __launch_bounds__(256, 4) k_serve(const gq_dev* __restrict__ fq, const __grid_constant__ ServeK a) {
+__global__ void __launch_bounds__(256, KIND == GQ_WFQ ? 0 : 4) k_serve(const gq_dev* __restrict__ fq, const __grid_constant__ ServeK a) {
     cg::cluster_group cluster = cg::this_cluster();
     const u32 cblocks = cluster.num_blocks();
     const u32 slot = blockIdx.x / cblocks;
@@ -278,15 +298,11 @@ __global__ void __launch_bounds__(256, 4) k_serve(const gq_dev* __restrict__ fq,
         u64* table = a.tables + lead * (chunk_map_bytes(kServeChunkCap) / 8);
         const gq_dev& qa = fq[2 * lead];
         const gq_dev& qb = fq[2 * lead + 1];
-        u32 levels;
-        if (members <= 1) {
-            levels = cluster_bfs<KIND>(qa, qb, lctl + 1, table, kServeChunkCap, g, dist, ct, nct, cluster, &edges,
-                                       a.stats + 2);
-        } else {
-            const GangSync sync{cluster, a.gang + 8 * (u64)lead, ctl + 6, members, ct == 0, a.wait_ns, a.stats + 2};
-            levels = group_bfs<KIND>(qa, qb, lctl + 1, table, kServeChunkCap, g, dist, rank * nct + ct,
-                                     members * nct, sync, &edges, a.stats + 2);
-        }
+        // a gang shares the leader's chunk map at full size; one cluster uses
+        // the cluster search's (its warps are busy with their own gathers)
+        const ServeSync sync{cluster, a.gang + 8 * (u64)lead, ctl + 6, members, ct == 0, a.wait_ns, a.stats + 2};
+        const u32 levels = group_bfs<KIND>(qa, qb, lctl + 1, table, members > 1 ? kServeChunkCap : kClusterChunkCap,
+                                           g, dist, rank * nct + ct, members * nct, sync, &edges, a.stats + 2);
         if (ct == 0 && t != kMember) {
             ServeEntry* e = a.ring + (t & a.ring_mask);
             __threadfence_system();
@@ -855,9 +871,10 @@ extern "C" int gq_serve(const gq_serve_config* cfg, gq_serve_result* res) {
     std::vector<u64> graph_charge(c.ngraphs), graph_dist(c.ngraphs);
     u64 nmax = 1;
     // Per-thread queue records (G-WFQ, G-WFQ-YMC) are counted for the threads
-    // that run a request: a cluster in the persistent scheduler, the whole
-    // cooperative grid of one gq_bfs launch otherwise (adaptive mode may run a
-    // request either way and counts the larger).
+    // that run a request: a cluster in the persistent scheduler (a gang of
+    // clusters for a graph large enough to form one), the whole cooperative
+    // grid of one gq_bfs launch otherwise (adaptive mode may run a request
+    // either way and counts the larger).
     u32 mt = c.cluster_blocks * 256;
     if (c.mode != GQ_SERVE_PERSISTENT) {
         uint64_t bt = 0;
@@ -869,8 +886,14 @@ extern "C" int gq_serve(const gq_serve_config* cfg, gq_serve_result* res) {
         u64 m = 0;
         if (cudaMemcpy(&m, x.d_offsets + x.n, sizeof(u64), cudaMemcpyDeviceToHost) != cudaSuccess)
             return res->status = GQ_ERR_CUDA;
+        // a request that may be served by a gang counts a gang's threads
+        u32 mtg = mt;
+        const u32 gang = c.gang_clusters ? c.gang_clusters : 16;
+        const u64 gmin = c.gang_min_vertices ? c.gang_min_vertices : (1u << 17);
+        if (c.mode != GQ_SERVE_PER_REQUEST && gang > 1 && x.n >= gmin && c.cluster_blocks * 256 * gang > mtg)
+            mtg = c.cluster_blocks * 256 * gang;
         uint64_t qb = 0;
-        s = gq_workspace_bytes(c.kind, queue_capacity(c.kind, x.n), 4, mt, nullptr, &qb);
+        s = gq_workspace_bytes(c.kind, queue_capacity(c.kind, x.n), 4, mtg, nullptr, &qb);
         if (s != GQ_OK) return res->status = s;
         graph_dist[g] = round256(4 * x.n);
         graph_charge[g] = 8 * (x.n + 1) + 4 * m + graph_dist[g] + 2 * qb;
