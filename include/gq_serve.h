@@ -4,15 +4,15 @@
  * Requests (graph id, source vertex) arrive at given times; each asks for the
  * hop distances of a level-synchronous BFS (Section V-B) on one graph of a
  * resident pool.  Two ways to serve them on one GPU:
- *   GQ_SERVE_PERSISTENT   one persistent device scheduler: thread-block
- *                         clusters claim request tickets from a device counter,
- *                         wait (bounded polling) until the host has published
- *                         the ticket in a request ring in mapped pinned memory
- *                         (system-scope release / acquire), run the BFS on the
- *                         cluster's own pair of frontier queues, and mark the
- *                         ring entry done (system-scope release), which the host
- *                         polls.  Requests that arrive while others run are
- *                         taken as soon as a cluster frees up.
+ *   GQ_SERVE_PERSISTENT   one persistent device scheduler: idle thread-block
+ *                         clusters poll (bounded) the request ring in mapped
+ *                         pinned memory for the next ticket the host has
+ *                         published (system-scope release / acquire), take it
+ *                         with a CAS on a device claim counter, run the BFS on
+ *                         the cluster's own pair of frontier queues, and mark
+ *                         the ring entry done (system-scope release), which the
+ *                         host polls.  Requests that arrive while others run
+ *                         are taken as soon as a cluster frees up.
  *   GQ_SERVE_PER_REQUEST  the plain form: one gq_bfs launch per request
  *                         (the whole GPU, one request at a time), in arrival
  *                         order on one stream; completion is an event the host
