@@ -45,6 +45,7 @@ CAPACITY = 1 << 20
 # operations of the headline launch (profiles/traffic_k_run_mixed_2p18.md).  The ring queues'
 # traffic is their workspace read once and does not scale with the operations, so it is not
 # extrapolated here.  Set an entry to None whenever that kernel changes.
+E2E_THREADS = 1 << 17   # records of the e2e queues (threads of their batch kernels)
 NCU_TRAFFIC = {"lfq": None, "wfq": None, "ymc": 4 * (240192768 + 156758528)}
 
 
@@ -676,25 +677,33 @@ def main():
     # One step: for every queue kind, pinned host -> device copy of 2^20 items,
     # gq_enqueue_batch, gq_dequeue_batch, device -> host copy of the values and
     # the counts.  Each kind runs on its own stream, so one kind's copies
-    # overlap another's kernels; the step ends when all streams are done.
+    # overlap another's kernels; the host reads every step's counts, one step
+    # behind the launches.
     e2e = None
     if not args.no_e2e:
         n = CAPACITY
         # queues of their own, sized for the batch (G-WFQ-YMC: a pool of 3 x 2^20 cells for the batch's 2^21
-        # tickets, not the headline's 1.3 x 10^8, whose reset alone would clear 3 GB per step);
-        # the batch kernels run at most one resident wave of threads
-        eq = {k: gq.Queue(k, CAPACITY if k != "ymc" else 3 * CAPACITY, 8, max_threads=1 << 20)
+        # tickets, not the headline's 1.3 x 10^8, whose reset alone would clear 3 GB per step); the batch
+        # kernels run at most one resident wave of threads and never more threads than records: 2^17
+        # records (the enqueue and dequeue rates peak at 2^17 - 2^18 threads, `phases`) keep each reset's
+        # record clear at 2 x 16 MiB for G-WFQ instead of 2 x 128 MiB
+        eq = {k: gq.Queue(k, CAPACITY if k != "ymc" else 3 * CAPACITY, 8, max_threads=E2E_THREADS)
               for k in kinds}
         streams = {k: torch.cuda.Stream(device=dev) for k in kinds}
         host_items = torch.arange(1, n + 1, dtype=torch.int64).pin_memory()
-        bufs = {k: {"out": torch.empty(n, dtype=torch.int64).pin_memory(),
-                    "cnt": torch.empty(2, dtype=torch.int64).pin_memory(),
+        # two sets of host result buffers: step s + 1 is launched before the
+        # host waits for step s's counts, so its copies must not land where
+        # the host is still reading
+        bufs = {k: {"out": [torch.empty(n, dtype=torch.int64).pin_memory() for _ in range(2)],
+                    "cnt": [torch.empty(2, dtype=torch.int64).pin_memory() for _ in range(2)],
+                    "done": [torch.cuda.Event() for _ in range(2)],
                     "d_items": torch.empty(n, dtype=torch.int64, device=dev),
                     "d_out": torch.empty(n, dtype=torch.int64, device=dev),
                     "d_cnt": torch.zeros(2, dtype=torch.int64, device=dev)} for k in kinds}
         torch.cuda.synchronize()
 
-        def e2e_step():
+        def e2e_launch(s):
+            par = s & 1
             for k in kinds:
                 b = bufs[k]
                 with torch.cuda.stream(streams[k]):
@@ -702,18 +711,28 @@ def main():
                     b["d_items"].copy_(host_items, non_blocking=True)
                     gq.gq_enqueue_batch(eq[k].handle, b["d_items"], n, None, b["d_cnt"][0:1])
                     gq.gq_dequeue_batch(eq[k].handle, b["d_out"], n, None, b["d_cnt"][1:2])
-                    b["out"].copy_(b["d_out"], non_blocking=True)
-                    b["cnt"].copy_(b["d_cnt"], non_blocking=True)
-            for k in kinds:
-                streams[k].synchronize()
-            return sum(int(bufs[k]["cnt"][0]) + int(bufs[k]["cnt"][1]) for k in kinds)
+                    b["out"][par].copy_(b["d_out"], non_blocking=True)
+                    b["cnt"][par].copy_(b["d_cnt"], non_blocking=True)
+                    b["done"][par].record(streams[k])
 
-        for _ in range(3):
-            assert e2e_step() == 2 * n * len(kinds)
+        def e2e_collect(s):
+            par = s & 1
+            tot = 0
+            for k in kinds:
+                bufs[k]["done"][par].synchronize()
+                tot += int(bufs[k]["cnt"][par][0]) + int(bufs[k]["cnt"][par][1])
+            return tot
+
+        for w in range(3):
+            e2e_launch(w)
+            assert e2e_collect(w) == 2 * n * len(kinds)
         t0 = time.perf_counter()
         tot = 0
-        for _ in range(args.steps):
-            tot += e2e_step()
+        e2e_launch(0)
+        for st in range(args.steps):
+            if st + 1 < args.steps:
+                e2e_launch(st + 1)
+            tot += e2e_collect(st)
         dt = time.perf_counter() - t0
         for k in kinds:
             assert eq[k].sync_status() == 0
@@ -721,8 +740,9 @@ def main():
         e2e = {"value": tot / dt / 1e6, "unit": "Mops/s", "h2d_bytes_per_step": 8 * n * len(kinds),
                "d2h_bytes_per_step": (8 * n + 16) * len(kinds),
                "how": "per queue kind on its own stream: reset, pinned H2D of 2^20 items, gq_enqueue_batch, "
-                      "gq_dequeue_batch, D2H of values and counts; the kinds' streams overlap; wall clock over "
-                      "%d steps" % args.steps}
+                      "gq_dequeue_batch, D2H of values and counts; the kinds' streams overlap, and step s + 1 is "
+                      "launched before the host waits for and reads step s's counts (two sets of host result "
+                      "buffers); wall clock over %d steps" % args.steps}
 
     apps = None
     if not args.no_apps:
