@@ -189,13 +189,14 @@ __global__ void __launch_bounds__(256) k_enqueue_batch(const __grid_constant__ g
     const u64 stride = (u64)gridDim.x * blockDim.x;
     const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
     u64 ok = 0;
-    for (u64 k = tid; k < n; k += stride) {
+    u32 seq = 0;     // the thread's operation index (G-WFQ counts its help delay by it)
+    for (u64 k = tid; k < n; k += stride, ++seq) {
         const T v = items[k];
         int s;
         if (KIND == GQ_YMC && sizeof(T) == 8 && (u64)v >= 0xFFFFFFFFFFFFFFFEull)
             s = GQ_ERR_RESERVED_VALUE;
         else
-            s = queue_enqueue<T, KIND>(q, v, tid);
+            s = queue_enqueue<T, KIND>(q, v, tid, nullptr, seq);
         if (status) status[k] = (int8_t)s;
         ok += (s == GQ_OK);
     }
@@ -224,13 +225,14 @@ __global__ void __launch_bounds__(256) k_dequeue_batch(const __grid_constant__ g
     T* my = stage[threadIdx.x >> 5];
     const bool vec = !(reinterpret_cast<uintptr_t>(status) & (V - 1)) && (blockDim.x & 31) == 0;
     const u64 tiles = vec ? n / (32 * V) : 0;
+    u32 seq = 0;     // the thread's operation index (G-WFQ counts its help delay by it)
     for (u64 w = tid >> 5; w < tiles; w += stride >> 5) {
         const u64 k0 = (w * 32 + lane) * V;
         T v[V];
         u32 packed = 0, got = 0;
 #pragma unroll
         for (u32 j = 0; j < V; ++j) {
-            const int s = queue_dequeue<T, KIND>(q, &v[got], tid);
+            const int s = queue_dequeue<T, KIND>(q, &v[got], tid, nullptr, seq++);
             got += (s == GQ_OK);
             packed |= (u32)(uint8_t)(int8_t)s << (8 * j);
         }
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(256) k_dequeue_batch(const __grid_constant__ g
     }
     for (u64 k = tiles * 32 * V + tid; k < n; k += stride) {
         T v;
-        const int s = queue_dequeue<T, KIND>(q, &v, tid);
+        const int s = queue_dequeue<T, KIND>(q, &v, tid, nullptr, seq++);
         if (status) status[k] = (int8_t)s;
         if (s == GQ_OK) {
             // compaction: the successful lanes of the warp take consecutive
