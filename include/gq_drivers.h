@@ -63,9 +63,9 @@ enum {
 enum {
     GQ_OC_TICKETS = 0,    /* tickets taken (per lane)                                     */
     GQ_OC_FAA = 1,        /* counter fetch-and-adds issued (one per WaveFAA batch)        */
-    GQ_OC_CAS = 2,        /* CAS attempts on slots / cells: install, repair, consume, claim */
+    GQ_OC_CAS = 2,        /* CAS attempts on slots / cells: install, repair, claim        */
     GQ_OC_CAS_FAIL = 3,   /* ... of which failed                                          */
-    GQ_OC_RMW = 4,        /* other slot RMWs (Consume's atomic-OR fallback)               */
+    GQ_OC_RMW = 4,        /* other slot RMWs (the ring Consume's atomic OR)               */
     GQ_OC_THRESHOLD = 5,  /* Threshold RMWs (reset, decrement; one per group of lanes)     */
     GQ_OC_CATCHUP = 6,    /* Tail catch-ups of EMPTY dequeues (one per group of lanes)     */
     GQ_OC_BURNED = 7,     /* tickets given up without an install or an item (RETRY/EMPTY) */

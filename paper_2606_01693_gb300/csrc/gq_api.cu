@@ -152,15 +152,15 @@ __global__ void k_reset_slots(gq_dev q, u64 base_ticket) {
     const u64 cm1 = (c0 - 1) & cmask;
     const u64 cm2 = (c0 - 2) & cmask;
     const u64 stride = (u64)gridDim.x * blockDim.x;
-    // empty slots start "consumed in the previous cycle" (BOTC, Note two cycles
-    // back), the value an enqueue predicts; BOTC and BOT are both empty
+    // empty slots start "emptied in the previous cycle" (BOT, Note two cycles
+    // back), the value an enqueue predicts
     for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < 2 * n; j += stride) {
         if (q.kind == GQ_LFQ) {
-            q.aq.slots[j] = lfq_entry(cm1, kSafe, kBotC);
-            q.fq.slots[j] = (j < n) ? lfq_entry(c0, kSafe, (u32)j) : lfq_entry(cm1, kSafe, kBotC);
+            q.aq.slots[j] = lfq_entry(cm1, kSafe, kBot);
+            q.fq.slots[j] = (j < n) ? lfq_entry(c0, kSafe, (u32)j) : lfq_entry(cm1, kSafe, kBot);
         } else {
-            q.aq.slots[j] = wfq_entry(cm2, cm1, 1, 1, kWBotC);
-            q.fq.slots[j] = (j < n) ? wfq_entry(cm1, c0, 1, 1, (u32)j) : wfq_entry(cm2, cm1, 1, 1, kWBotC);
+            q.aq.slots[j] = wfq_entry(cm2, cm1, 1, 1, kWBot);
+            q.fq.slots[j] = (j < n) ? wfq_entry(cm1, c0, 1, 1, (u32)j) : wfq_entry(cm2, cm1, 1, 1, kWBot);
         }
     }
 }

@@ -9,11 +9,12 @@
 //     bit  32      Safe
 //     bits 31..0   Index:  a value < 2^32 - 2,  BOT = 2^32 - 1 (empty),
 //                          BOTC = 2^32 - 2 (consumed)
-// Consume marks the index field BOTC and keeps the Cycle and Safe bits: a CAS
-// from the entry the dequeuer read to the same entry with index BOTC, falling
-// back to an atomic OR of BOTC into the index bits (any index then becomes
-// BOTC or BOT, both of the "empty class") if a concurrent Safe change made the
-// CAS fail.  Writing exactly BOTC keeps a consumed slot's value predictable.
+// Consume empties the index field and keeps the Cycle and Safe bits: one
+// atomic OR of all ones into the index bits, so a consumed slot always reads
+// <cycle, Safe, BOT> (BOT and BOTC are both of the "empty class"; the ring
+// treats them alike).  While a slot holds a live index only its consumer
+// changes the index bits (others CAS the Safe bit), so the OR needs no expected
+// value and returns nothing: the dequeuer does not wait for it.
 // Cycles are compared modulo R (a is older than b iff 0 < (b - a) mod R < R/2),
 // sound while the live skew on a slot stays below R/2 (Lemma "Reduced-width
 // cycle tags").
@@ -31,8 +32,8 @@
 //     cache-line remapping of consecutive tickets is deliberately not used;
 //   * a CAS that fails on a slot re-evaluates the same ticket with the value it
 //     returned (no ticket is burned for a lost race on a still-usable slot);
-//   * an enqueue first CASes against the slot's most likely value, "consumed in
-//     the previous cycle" <c-1, Safe, BOTC>, instead of loading it: a right
+//   * an enqueue first CASes against the slot's most likely value, "emptied in
+//     the previous cycle" <c-1, Safe, BOT>, instead of loading it: a right
 //     guess saves one L2 round trip, a wrong one returns the current value,
 //     which the protocol then evaluates exactly as a load's result.
 #pragma once
@@ -179,7 +180,7 @@ __device__ int lfq_ring_enq(const gq_dev& q, const gq_ring_view& r, u32 idx, u64
         u64* slot = r.slots + (t & q.slot_mask);
         const u64 c = (t >> q.ring_order) & q.cycle_mask;
         const u64 ne = lfq_entry(c, kSafe, idx);
-        u64 e = lfq_entry((c - 1) & q.cycle_mask, kSafe, kBotC);   // predicted current value
+        u64 e = lfq_entry((c - 1) & q.cycle_mask, kSafe, kBot);    // predicted current value
         bool done = cas(slot, e, ne);
         oc_cas<CNT>(done);
         for (; !done && it < kRetryLimit; ++it) {
@@ -225,13 +226,10 @@ __device__ int lfq_ring_deq(const gq_dev& q, const gq_ring_view& r, u32* idx, u6
                 if (lfq_index(e) < kBotC) {          // Consume and return the index
                     *idx = lfq_index(e);
                     if (tk) *tk = h;
-                    // relaxed: the acquire load of e already ordered the payload read
-                    const bool ok = aref<u64>(*slot).compare_exchange_strong(e, (e & ~0xFFFFFFFFull) | kBotC, kRlx, kRlx);
-                    oc_cas<CNT>(ok);
-                    if (!ok) {
-                        oc_add<CNT>(kOcRmw);
-                        aref<u64>(*slot).fetch_or(kBotC, kRlx);
-                    }
+                    // relaxed: the acquire load of e already ordered the payload
+                    // read; the release CAS that hands the index on orders the OR
+                    red_or_rlx(slot, kBot);
+                    oc_add<CNT>(kOcRmw);
                     return GQ_OK;
                 }
                 break;

@@ -57,8 +57,8 @@ __global__ void k_static_init(gq_dev q, unsigned long long* num_out) {
     const u64 c0 = (2 * n >> (q.log2n + 1)) & ((1ull << q.cycle_bits) - 1);   // cycle of ticket 2n
     const u64 cm1 = (c0 - 1) & ((1ull << q.cycle_bits) - 1);
     for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < 2 * n; j += stride) {
-        q.aq.slots[j] = lfq_entry(cm1, kSafe, kBotC);
-        q.fq.slots[j] = (j < n) ? lfq_entry(c0, kSafe, (u32)j) : lfq_entry(cm1, kSafe, kBotC);
+        q.aq.slots[j] = lfq_entry(cm1, kSafe, kBot);
+        q.fq.slots[j] = (j < n) ? lfq_entry(c0, kSafe, (u32)j) : lfq_entry(cm1, kSafe, kBot);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *q.err = 0;

@@ -279,7 +279,7 @@ __device__ int wfq_try_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u64*
     const u64 c = (t >> q.ring_order) & q.cycle_mask;
     // predicted current value: consumed in the previous cycle, Note one older
     const u64 cm1 = (c - 1) & q.cycle_mask;
-    u64 e = wfq_entry((c - 2) & q.cycle_mask, cm1, 1, 1, kWBotC);
+    u64 e = wfq_entry((c - 2) & q.cycle_mask, cm1, 1, 1, kWBot);
     bool done = cas(slot, e, wfq_entry(cm1, c, 1, 1, idx));
     oc_cas<CNT>(done);
     for (u32 it = 0; !done && it < kRetryLimit; ++it) {
@@ -297,8 +297,10 @@ __device__ int wfq_try_enq(const gq_ring_view& R, const gq_dev& q, u32 idx, u64*
 }
 
 // Consumes the item of ticket h in `slot` (its cycle already checked).
-// Consume: index field to BOTC, other fields kept (CAS from the entry read,
-// OR as the fallback); e was read with acquire, so the consume can be relaxed.
+// Consume: index field to BOT, other fields kept, by one atomic OR that
+// returns nothing (while the slot holds the item only its consumer changes the
+// index bits; helpers and finalisers CAS the other fields); e was read with
+// acquire, so the consume can be relaxed.
 template <bool CNT = false>
 __device__ __forceinline__ u32 wfq_consume(const gq_ring_view& R, u64* slot, u64 e, u64 h, const gq_dev& q) {
     if (!(e & kWEnq)) {
@@ -306,12 +308,8 @@ __device__ __forceinline__ u32 wfq_consume(const gq_ring_view& R, u64* slot, u64
         e |= kWEnq;
     }
     const u32 i = w_idx(e);
-    const bool ok = aref<u64>(*slot).compare_exchange_strong(e, (e & ~(u64)kWIdxMask) | kWBotC, kRlx, kRlx);
-    oc_cas<CNT>(ok);
-    if (!ok) {
-        oc_add<CNT>(kOcRmw);
-        aref<u64>(*slot).fetch_or(kWBotC, kRlx);
-    }
+    red_or_rlx(slot, kWIdxMask);
+    oc_add<CNT>(kOcRmw);
     return i;
 }
 

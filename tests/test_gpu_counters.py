@@ -5,8 +5,8 @@ driver.
 Pins:
   * one thread, enqueue-then-dequeue pairs: the counts have a closed form --
     G-LFQ / G-WFQ: per pair four tickets, four fetch-and-adds (a batch of one
-    lane), four successful CASes (fq consume, aq install, aq consume, fq
-    install), two first loads of a slot, and one Threshold reset over the
+    lane), two successful CASes (aq install, fq install), two Consume ORs
+    (fq, aq), two first loads of a slot, and one Threshold reset over the
     whole run (aq's Threshold starts at -1, the first install sets it to
     3n - 1 and it never moves again); G-WFQ-YMC: per pair two tickets, two
     successful CASes (the value, the dequeue's claim) and one cell load;
@@ -14,7 +14,7 @@ Pins:
     up (tickets - burned = ring steps = 2 per successful operation for the
     rings, 1 for G-WFQ-YMC, while no operation goes slow); WaveFAA issues
     between tickets / 32 and tickets fetch-and-adds; every completed step is
-    one successful CAS (or Consume's OR fallback); and the counting
+    one successful CAS or one Consume OR; and the counting
     instantiation still passes the run-log checks against the oracle.
 """
 import numpy as np
@@ -70,7 +70,7 @@ def test_single_thread_pairs_closed_form(kind):
         want = {"tickets": K, "faa": K, "cas": K, "cas_fail": 0, "rmw": 0, "threshold": 0, "catchup": 0,
                 "burned": 0, "loads": K // 2, "slow": 0, "spin": 0, "marked": 0}
     else:
-        want = {"tickets": 2 * K, "faa": 2 * K, "cas": 2 * K, "cas_fail": 0, "rmw": 0, "threshold": 1,
+        want = {"tickets": 2 * K, "faa": 2 * K, "cas": K, "cas_fail": 0, "rmw": K, "threshold": 1,
                 "catchup": 0, "burned": 0, "loads": K, "slow": 0, "spin": 0, "marked": 0}
     assert oc == want
 
