@@ -46,7 +46,7 @@ CAPACITY = 1 << 20
 # traffic is their workspace read once and does not scale with the operations, so it is not
 # extrapolated here.  Set an entry to None whenever that kernel changes.
 E2E_THREADS = 1 << 17   # records of the e2e queues (threads of their batch kernels)
-NCU_TRAFFIC = {"lfq": None, "wfq": None, "ymc": 4 * (240192768 + 156758528)}
+NCU_TRAFFIC = {"lfq": None, "wfq": None, "ymc": None}
 
 
 def parse():

@@ -60,6 +60,12 @@ constexpr u32 kYWaitPolls = 256; // then, if T shows the ticket taken, polls 64 
 // patience 0 scanned more than 2^16 cells).  The bound only stops a search that
 // has run through millions of cells.
 constexpr u32 kYScanLimit = 1u << 22;
+// Cells ahead of its own ticket that a fast enqueue asks L2 to prefetch.  The
+// pool is touched once per ticket and is far larger than L2, so a cell's first
+// access (the enqueue's CAS, or an early dequeuer's read) would otherwise miss
+// to DRAM on the operation's dependent chain; T reaches ticket i + kYPrefetch
+// a few microseconds later, by which time the line is in L2.
+constexpr u64 kYPrefetch = 1ull << 15;
 
 enum : int {
     kYErId = 0,    // enqueue request: > 0 pending from cell id on, < 0 done at cell -id
@@ -275,6 +281,8 @@ __device__ int ymc_enqueue(const gq_dev& q, T v, u32 tid, u64* tk = nullptr) {
     for (u32 p = 0; p <= q.patience_enq; ++p) {
         const u64 i = warp_faa<MATCH, CNT>(q.ymc_tail, 1, q.batch_width);
         if (!ycell_ok(q, i)) return GQ_ERR_POOL_EXHAUSTED;
+        if (i + kYPrefetch <= q.capacity)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(yval(q, i + kYPrefetch)));
         u64 b = kVBot;
         const bool ok = aref<u64>(*yval(q, i)).compare_exchange_strong(b, x, kRel, kRlx);
         oc_cas<CNT>(ok);
