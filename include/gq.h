@@ -144,6 +144,9 @@ typedef struct {
     unsigned long long* cell_deq;   /* dequeue references: cell i at cell_deq[2 i]
                                        (= cell_val[2 i + 1], one 16-byte pair)     */
     unsigned long long* ymc_rec;    /* per-thread handles and requests             */
+    unsigned long long* ymc_hw;     /* highest cell a slow dequeue's candidate search
+                                       visited since the last reset (with T and H it
+                                       bounds the cells gq_reset clears)            */
 } gq_dev;
 
 /* Bytes of device workspace gq_create needs for this configuration, so a caller

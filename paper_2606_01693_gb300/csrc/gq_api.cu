@@ -122,6 +122,7 @@ __global__ void k_reset_ctrl(gq_dev q, u64 base_ticket) {
     if (q.kind == GQ_YMC) {
         *q.ymc_tail = 1;
         *q.ymc_head = 1;
+        *q.ymc_hw = 0;
         return;
     }
     if (q.kind == GQ_LFQ) {
@@ -165,13 +166,25 @@ __global__ void k_reset_slots(gq_dev q, u64 base_ticket) {
     }
 }
 
-// G-WFQ-YMC cells: every <value, dequeue reference> pair = <BOT, BOT>, one
-// 16-byte store per cell, grid-stride.
-__global__ void k_reset_cells(unsigned long long* pairs, u64 cells) {
-    ulonglong2* p = reinterpret_cast<ulonglong2*>(pairs);
+// G-WFQ-YMC cells: every <value, dequeue reference> pair = <BOT, BOT> (one
+// 16-byte store per cell) and every enqueue reference = 0, grid-stride.  With
+// `known`, only the cells used since the last reset: tickets below T and H
+// (every fast path and slow enqueue takes its cell from them) and cells up to
+// the slow dequeues' search mark; the rest are still clear.  The first reset
+// of a workspace clears all of them.
+__global__ void k_reset_cells(gq_dev q, bool known) {
+    u64 cells = q.capacity + 1;
+    if (known) {
+        const u64 used = max(max(*q.ymc_tail, *q.ymc_head), *q.ymc_hw + 1);
+        cells = min(cells, used);
+    }
+    ulonglong2* p = reinterpret_cast<ulonglong2*>(q.cell_val);
     const ulonglong2 e = make_ulonglong2(kVBot, kRefBot);
     const u64 stride = (u64)gridDim.x * blockDim.x;
-    for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < cells; j += stride) p[j] = e;
+    for (u64 j = (u64)blockIdx.x * blockDim.x + threadIdx.x; j < cells; j += stride) {
+        p[j] = e;
+        q.cell_enq[j] = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -338,9 +351,9 @@ extern "C" int gq_reset(gq_handle h, void* stream) {
         // eight 256-thread blocks per SM: one resident wave of the fill
         const uint64_t sms = h->sm_count > 0 ? (uint64_t)h->sm_count : 1;
         const uint64_t blocks = std::min<uint64_t>((cells + 255) / 256, 8 * sms);
-        k_reset_cells<<<(uint32_t)blocks, 256, 0, st>>>(d.cell_val, cells);
+        k_reset_cells<<<(uint32_t)blocks, 256, 0, st>>>(d, h->ymc_pool_known);
         if (cudaGetLastError() != cudaSuccess) return GQ_ERR_CUDA;
-        if (cudaMemsetAsync(d.cell_enq, 0, cells * 8, st) != cudaSuccess) return GQ_ERR_CUDA;
+        h->ymc_pool_known = true;
         if (cudaMemsetAsync(d.ymc_rec, 0, (uint64_t)d.max_threads * kYmcRecBytes, st) != cudaSuccess)
             return GQ_ERR_CUDA;
     } else {
@@ -425,6 +438,7 @@ extern "C" int gq_create(int kind, uint64_t capacity, uint32_t elem_bytes, uint3
     if (kind == GQ_YMC) {
         d.ymc_tail = at<unsigned long long>(b, h->lay.ctrl + kCtlYmcTail * kCtlStride);
         d.ymc_head = at<unsigned long long>(b, h->lay.ctrl + kCtlYmcHead * kCtlStride);
+        d.ymc_hw = at<unsigned long long>(b, h->lay.ctrl + kCtlYmcHw * kCtlStride);
         d.cell_val = at<unsigned long long>(b, h->lay.cell_val);
         d.cell_enq = at<unsigned long long>(b, h->lay.cell_enq);
         d.cell_deq = at<unsigned long long>(b, h->lay.cell_deq);

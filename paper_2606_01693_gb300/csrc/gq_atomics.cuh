@@ -56,6 +56,11 @@ __device__ __forceinline__ i64 faa(i64* p, i64 v) { return aref<i64>(*p).fetch_a
 __device__ __forceinline__ u64 fetch_or(u64* p, u64 v) { return aref<u64>(*p).fetch_or(v, kAR); }
 __device__ __forceinline__ u64 fetch_and(u64* p, u64 v) { return aref<u64>(*p).fetch_and(v, kAR); }
 __device__ __forceinline__ i64 exch(i64* p, i64 v) { return aref<i64>(*p).exchange(v, kAR); }
+// Relaxed atomic maximum that returns nothing.
+__device__ __forceinline__ void red_max_rlx(u64* p, u64 v) {
+    asm volatile("red.relaxed.gpu.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // Relaxed atomic OR that returns nothing (a reduction): the issuing thread does
 // not wait for it.  Later release operations of the thread still order it.
 __device__ __forceinline__ void red_or_rlx(u64* p, u64 v) {

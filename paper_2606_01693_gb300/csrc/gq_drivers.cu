@@ -161,14 +161,17 @@ __global__ void k_drain(const __grid_constant__ gq_dev q, u64* out, u64 max, uns
 template <class T, int KIND, bool REC, bool CNT>
 int launch_run(gq_queue* h, const RunK& a, u32 block, cudaStream_t st) {
     const u32 grid = (a.threads + block - 1) / block;
-    // G-LFQ on a grid of at least two waves at 768 threads per SM: reserve
-    // (unused) dynamic shared memory so that only 768 threads per SM are
-    // resident.  Fewer threads contend for the Head / Tail / Threshold lines at
-    // once and the ring's CAS retries drop; the blocks beyond the first wave
-    // start as earlier ones finish.  G-WFQ and G-WFQ-YMC run slower with the
-    // cap, and so does a grid that would fit in one uncapped wave.
+    // G-LFQ with more threads than ring capacity, on a grid of at least two
+    // waves at 768 threads per SM: reserve (unused) dynamic shared memory so
+    // that only 768 threads per SM are resident.  Oversubscribed rings run
+    // near full or near empty, where the threads meet on the Head / Tail /
+    // Threshold lines and on each other's slots; fewer of them at once give
+    // up fewer tickets.  The blocks beyond the first wave start as earlier
+    // ones finish.  A ring with a slot for every thread (the balanced
+    // workloads) runs faster uncapped, and so do G-WFQ, G-WFQ-YMC and a grid
+    // that would fit in one uncapped wave.
     size_t smem = 0;
-    if (KIND == GQ_LFQ) {
+    if (KIND == GQ_LFQ && (u64)a.threads > h->dev.capacity) {
         const u32 per_sm = block >= 768 ? 1u : 768u / block;
         if ((u64)grid >= 2ull * per_sm * (u64)h->sm_count && h->smem_per_sm > 0) {
             // a block's footprint halfway between sm/(per_sm + 1) and sm/per_sm:

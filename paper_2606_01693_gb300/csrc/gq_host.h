@@ -34,6 +34,7 @@ enum {
     kCtlFqHead = 5, kCtlFqTail = 6, kCtlFqThr = 7,
     kCtlYmcTail = 8, kCtlYmcHead = 9,
     kCtlAqSlow = 10, kCtlFqSlow = 11,
+    kCtlYmcHw = 12,
     kCtlLines = 16
 };
 
@@ -49,6 +50,7 @@ struct gq_queue {
     uint64_t start_ticket;
     void* aux;            // library-owned device scratch of the applications (gq_bfs), made on first use
     uint64_t aux_bytes;
+    bool ymc_pool_known = false;   // G-WFQ-YMC: T, H and the scan mark bound the used cells (after the first reset)
 };
 
 // Status helpers

@@ -240,12 +240,18 @@ static __device__ __noinline__ void ymc_help_deq(const gq_dev& q, u32 me, u32 p)
         u32 jt = 0;
         for (; jt < kYScanLimit && idx == old && cand == 0; ++jt) {
             ++i;
-            if (!ycell_ok(q, (u64)i)) return;
+            if (!ycell_ok(q, (u64)i)) {
+                red_max_rlx(q.ymc_hw, (u64)(i - 1));
+                return;
+            }
             u64 v;
             const int s = ymc_help_enq(q, me, (u64)i, &v);
             if (s == kYEmpty || (s == kYValue && ld_acq(ydeq(q, i)) == kRefBot)) cand = i;
             else idx = ld_i(dr + kYDrIdx);
         }
+        // The search may have settled cells above T and H (marked them
+        // unusable, attached requests): the reset must clear them too.
+        if (jt) red_max_rlx(q.ymc_hw, (u64)i);
         if (jt == kYScanLimit) break;   // never claim the request's own first cell unannounced
         if (cand != 0) {
             u64 cur = (u64)idx;

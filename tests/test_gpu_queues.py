@@ -274,24 +274,28 @@ def test_caller_owned_workspace(kind):
 
 
 def test_capped_run_captured_in_a_graph():
-    # a G-LFQ run of 2^18 threads (1024 blocks) is launched with the residency
-    # cap; made only inside stream capture, it replays like an eager launch
-    # (pairs: zero FULL, zero EMPTY, sums agree)
-    T = 1 << 18
-    q = make_queue("lfq", T, 8, max_threads=T)
+    # a G-LFQ run of 2^18 threads (1024 blocks) on a ring of capacity 2^16 is
+    # launched with the residency cap (more threads than slots); made only
+    # inside stream capture, it replays like an eager launch: every attempt is
+    # counted once and what was enqueued and not dequeued is what remains
+    T, total, cap = 1 << 18, 1 << 20, 1 << 16
+    q = make_queue("lfq", cap, 8, max_threads=T)
     counts = torch.zeros(8, dtype=torch.int64, device=DEV)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         q.reset()
         counts.zero_()
-        gq.gq_run(q.handle, gq.GQ_RUN_PAIRS, T, block=256, ops=4, counts=counts)
+        gq.gq_run(q.handle, gq.GQ_RUN_SPLIT, T, block=256, producers=T // 2, total_ops=total, counts=counts)
     for _ in range(3):
         g.replay()
         torch.cuda.synchronize()
         c = u64(counts)
-        assert c[gq.GQ_CNT_ENQ_OK] == 2 * T and c[gq.GQ_CNT_DEQ_OK] == 2 * T, c
-        assert c[gq.GQ_CNT_ENQ_FULL] == 0 and c[gq.GQ_CNT_DEQ_EMPTY] == 0 and c[gq.GQ_CNT_ERRORS] == 0
-        assert c[gq.GQ_CNT_SUM_ENQ] == c[gq.GQ_CNT_SUM_DEQ]
+        assert c[gq.GQ_CNT_ERRORS] == 0, c
+        assert c[gq.GQ_CNT_ENQ_OK] + c[gq.GQ_CNT_ENQ_FULL] + c[gq.GQ_CNT_DEQ_OK] + c[gq.GQ_CNT_DEQ_EMPTY] == total
+        assert c[gq.GQ_CNT_ENQ_OK] > 0 and c[gq.GQ_CNT_DEQ_OK] > 0
+        left = drain(q, cap)
+        assert len(left) == int(c[gq.GQ_CNT_ENQ_OK] - c[gq.GQ_CNT_DEQ_OK])
+        assert (int(c[gq.GQ_CNT_SUM_ENQ]) - int(c[gq.GQ_CNT_SUM_DEQ])) % (1 << 64) == int(left.sum(dtype=np.uint64))
     assert q.sync_status() == 0
 
 

@@ -1,5 +1,8 @@
 """G-WFQ-YMC specifics on the GPU against the oracle (run with -m gpu): the
-slow paths (patience 0), the cell-pool bound, and the reserved payload codes."""
+slow paths (patience 0), the cell-pool bound, the reserved payload codes, and
+the reset that clears only the cells an episode used."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -100,3 +103,58 @@ def test_slow_dequeues_on_an_empty_heavy_split(T):
     assert rep["violations"] == 0, str(rep)
     assert r["counts"][gq.GQ_CNT_ERRORS] == 0
     assert rep["deq_empty"] > 0
+
+
+class _RingView(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("head", "tail", "threshold", "slots", "rec", "owner", "helpc",
+                                                "slow_pending")]
+
+
+class _DevView(ctypes.Structure):
+    """Mirror of gq_dev (include/gq.h), to find the pool inside a caller-owned workspace."""
+    _fields_ = ([(n, ctypes.c_uint32) for n in ("kind", "elem_bytes", "log2n", "cycle_bits", "max_threads",
+                                                 "patience_enq", "patience_deq", "help_delay", "batch_width",
+                                                 "ring_order", "backoff_ns", "due_wait", "patience_stretch",
+                                                 "reserved1")]
+                + [(n, ctypes.c_uint64) for n in ("capacity", "slot_mask", "cycle_mask", "cycle_half", "thr_reset")]
+                + [("aq", _RingView), ("fq", _RingView)]
+                + [(n, ctypes.c_void_p) for n in ("data", "err", "scratch", "ymc_tail", "ymc_head", "cell_val",
+                                                   "cell_enq", "cell_deq", "ymc_rec", "ymc_hw")])
+
+
+def test_reset_clears_every_cell_an_episode_touched():
+    """gq_reset clears only the cells used since the previous reset: those below
+    T and H and those the slow dequeues' candidate searches reached (the search
+    mark).  After episodes whose searches run past T and H (90 % consumers,
+    patience 0), every cell of the pool is clear again, and the reused pool
+    gives runs that pass the run-log checks."""
+    T, cap = 1 << 12, 1 << 22
+    q = gq.Queue("ymc", cap, 8, max_threads=T, use_torch_memory=True, patience_enq=0, patience_deq=0)
+    assert ctypes.sizeof(_DevView) <= gq.GQ_VIEW_BYTES
+    view = _DevView()
+    assert gq.load().gq_device_view(q.handle, ctypes.byref(view)) == 0
+    assert view.capacity == cap
+    base = (q._ws.data_ptr() + 255) // 256 * 256
+    ws = q._ws[base - q._ws.data_ptr():]
+    u64view = lambda ptr, n: ws[ptr - base: ptr - base + 8 * n].view(torch.int64)   # noqa: E731
+    pairs = u64view(view.cell_val, 2 * (cap + 1)).view(cap + 1, 2)
+    enq = u64view(view.cell_enq, cap + 1)
+    ctl = lambda ptr: int(u64view(ptr, 1).item()) & ((1 << 64) - 1)   # noqa: E731
+    P = T // 10
+    for episode in range(3):
+        r = run_log(q, gq.GQ_RUN_SPLIT, T, producers=P, total_ops=24 * T)
+        left = drain(q, 24 * T)
+        rep = oracle.check_log(r["kind"], r["status"], r["val"], left)
+        assert rep["violations"] == 0, (episode, str(rep))
+        torch.cuda.synchronize()
+        t, h, hw = ctl(view.ymc_tail), ctl(view.ymc_head), ctl(view.ymc_hw)
+        assert hw > 0 and max(t, h, hw + 1) <= cap + 1
+        touched = (pairs[:, 0] != -1) | (pairs[:, 1] != 0) | (enq != 0)
+        assert int(touched.sum().item()) > 0
+        hi = int(torch.nonzero(touched).max().item())
+        assert hi < max(t, h, hw + 1), (hi, t, h, hw)     # the bound covers every touched cell
+        q.reset()
+        torch.cuda.synchronize()
+        assert ctl(view.ymc_hw) == 0 and ctl(view.ymc_tail) == 1
+        assert bool((pairs[:, 0] == -1).all()) and bool((pairs[:, 1] == 0).all()) and bool((enq == 0).all())
+    q.close()
