@@ -37,16 +37,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "queue Mops/s (enq+deq) vs threads; % of measured L2-atomic peak; serving p99"
 CAPACITY = 1 << 20
-# DRAM bytes (read + write) per launch of each run kernel at the headline size.  G-WFQ-YMC: one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one kernel, one launch) of the
-# 2^18-thread case of the same workload, `bench.py --threads 262144 --steps 1 --warmup 1
-# --no-sweep --no-e2e --no-cpu --no-apps --no-batched --no-serving --kinds ymc`: 240192768 +
-# 156758528 bytes for 26.2 M operations (each ticket's cell touched once), scaled by the 4x
-# operations of the headline launch (profiles/traffic_k_run_mixed_2p18.md).  The ring queues'
-# traffic is their workspace read once and does not scale with the operations, so it is not
-# extrapolated here.  Set an entry to None whenever that kernel changes.
+# DRAM bytes (read + write) per launch of each run kernel at the headline size, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, one kernel, one launch; profiles/
+# traffic_k_run_mixed_2p18.md).  G-WFQ: captured at the headline size itself (`bench.py
+# --no-sweep --no-e2e --no-cpu --no-apps --no-batched --no-serving --kinds wfq --steps 1
+# --warmup 1`; a one-pass metric set): 391.11 + 113.24 MB as ncu printed them.  G-WFQ-YMC: its
+# 2^18-thread case (`... --threads 262144 --kinds ymc`), 240533760 + 156694272 bytes for 26.2 M
+# operations (each ticket's cell touched once, so the bytes grow with the operations), scaled by
+# the 4x operations of the headline launch.  G-LFQ's traffic is its workspace read once and does
+# not grow with the operations; it has no headline-size capture.  Set an entry to None whenever
+# that kernel changes.
 E2E_THREADS = 1 << 17   # records of the e2e queues (threads of their batch kernels)
-NCU_TRAFFIC = {"lfq": None, "wfq": None, "ymc": None}
+NCU_TRAFFIC = {"lfq": None, "wfq": 391110000 + 113240000, "ymc": 4 * (240533760 + 156694272)}
 
 
 def parse():
