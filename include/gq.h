@@ -178,7 +178,9 @@ int gq_destroy(gq_handle h);
 
 /* Returns the queue to its freshly created empty state, asynchronously on
  * `stream`, and clears the device error word.  Must not overlap other calls on
- * the handle. */
+ * the handle.  G-WFQ-YMC: clears only the pool cells used since the previous
+ * reset (the first reset after gq_create clears the whole pool), so its cost
+ * follows the tickets taken, not the pool size. */
 int gq_reset(gq_handle h, void* stream);
 
 /* Enqueues d_items[0..n) (elem_bytes each), one attempt per item, concurrently
